@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs shaped like the phi-SfT sequences (no physics here).
+
+This module only *generates inputs*: grid meshes, pin masks, material values and
+external-force fields drawn from fixed seeds.  It holds none of the simulator's
+arithmetic (no mass lumping, no forces, no solves), so both the CUDA path and the
+FP64 oracle can be fed from it without sharing method code.
+
+Sheets are 1 m squares in the z = 0 plane, gravity along -z, "top" is the edge
+y = 1 m; an N x N grid has vertex (i, j) at (i/(N-1), j/(N-1), 0), index j*N + i,
+and each cell is split along alternating diagonals by the parity of i + j.
+The paper's own sequences (~300 vertices, ~40 frames, 55-95 cm cloths, Sec. 4.1)
+are not available; these grids stand in for them.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GRAVITY = (0.0, 0.0, -9.8)
+BASE_MATERIAL = (1.0e3, 0.3, 1.0e-4, 0.1)  # Y [N/m], nu, k_b [N m], rho [kg/m^2]
+
+
+def grid_mesh(N: int, size: float = 1.0):
+    """Regular N x N vertex grid, 2 (N-1)^2 triangles with alternating diagonals.
+
+    Returns (rest [n,3] float64, tris [m,3] int32), counter-clockwise seen from +z.
+    """
+    if N < 2:
+        raise ValueError("grid needs at least 2 vertices per side")
+    s = np.linspace(0.0, size, N)
+    X, Yg = np.meshgrid(s, s, indexing="xy")  # X[j, i] = s[i], Y[j, i] = s[j]
+    rest = np.stack([X.ravel(), Yg.ravel(), np.zeros(N * N)], axis=1)
+    tris = []
+    for j in range(N - 1):
+        for i in range(N - 1):
+            v00, v10, v01, v11 = j * N + i, j * N + i + 1, (j + 1) * N + i, (j + 1) * N + i + 1
+            if (i + j) % 2 == 0:
+                tris.append((v00, v10, v11))
+                tris.append((v00, v11, v01))
+            else:
+                tris.append((v00, v10, v01))
+                tris.append((v10, v11, v01))
+    return rest, np.asarray(tris, dtype=np.int32)
+
+
+def pins(N: int, kind: str):
+    """Pinned-vertex mask for an N x N grid.
+
+    'top2'  : the two corners of the top edge (y = 1)
+    'top'   : the whole top edge
+    'corners': all four corners
+    'none'  : nothing pinned
+    """
+    p = np.zeros(N * N, np.uint8)
+    top = (N - 1) * N
+    if kind == "top2":
+        p[top] = 1
+        p[top + N - 1] = 1
+    elif kind == "top":
+        p[top:top + N] = 1
+    elif kind == "corners":
+        p[[0, N - 1, top, top + N - 1]] = 1
+    elif kind != "none":
+        raise ValueError(kind)
+    return p
+
+
+def gaussian_forces(n: int, steps: int, sigma: float, seed: int = 0):
+    """Per-step, per-vertex, per-axis i.i.d. N(0, sigma) force in newtons, [steps, n, 3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.normal(0.0, sigma, size=(steps, n, 3))
+
+
+def sinusoid_wind(rest, steps: int, dt: float, amplitude: float, cell_area: float, seed: int = 0, K: int = 8):
+    """Smooth wind: sum of K seeded travelling sinusoids, [steps, n, 3] newtons.
+
+    F_i(t) = cell_area * sum_k (amplitude / K) d_k sin(kappa_k . X_i + omega_k t + phi_k),
+    d_k random unit vectors, |kappa_k| <= 4 pi / m, omega_k <= 4 pi / s, phi_k in [0, 2 pi).
+    ``amplitude`` is a pressure in N/m^2; each vertex carries one grid cell of area.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.normal(size=(K, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    kdir = rng.normal(size=(K, 3))
+    kdir /= np.linalg.norm(kdir, axis=1, keepdims=True)
+    kappa = kdir * rng.uniform(0.0, 4.0 * math.pi, size=(K, 1))
+    omega = rng.uniform(0.0, 4.0 * math.pi, size=K)
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=K)
+    t = np.arange(steps) * dt
+    arg = (rest @ kappa.T)[None, :, :] + omega[None, None, :] * t[:, None, None] + phase[None, None, :]
+    return cell_area * (amplitude / K) * np.einsum("tnk,kc->tnc", np.sin(arg), d)
+
+
+@dataclasses.dataclass
+class Sheet:
+    N: int
+    rest: np.ndarray       # [n, 3]
+    tris: np.ndarray       # [m, 3] int32
+    pinned: np.ndarray     # [n] uint8
+    material: np.ndarray   # [4] Y, nu, kb, rho
+    forces: np.ndarray | None  # [steps, n, 3] or None
+
+    @property
+    def n(self):
+        return self.rest.shape[0]
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    sheets: list
+    dt: float
+    steps: int
+    precision: str         # "f32" or "f64"
+    cg_tol: float
+    cg_max_iter: int = 2000
+    checkpoint_every: int = 0
+    loss: str = "l2"       # "l2" (target trajectory) or "pinhole"
+    target_scale: tuple = (2.0, 1.0, 0.5, 1.0)  # target made with Y x2, kb x0.5
+    camera: tuple = (500.0, 0.5, 0.5, 2.0)      # f px, camera centre (x, y, z)
+
+    @property
+    def total_vertices(self):
+        return sum(s.n for s in self.sheets)
+
+
+def _sheet(N, pin, material, forces=None):
+    rest, tris = grid_mesh(N)
+    return Sheet(N, rest, tris, pins(N, pin), np.asarray(material, np.float64), forces)
+
+
+def config1():
+    """10x10 grid, two top corners pinned, FP64, 20 steps dt=1/30, CG tol 1e-10."""
+    return Workload("grid10_fp64_20steps", [_sheet(10, "top2", BASE_MATERIAL)], 1.0 / 30.0, 20, "f64", 1e-10)
+
+
+def config2(force_reading="area", force_sigma=0.05, steps=60):
+    """32x32 grid, top edge pinned, FP32, 60 steps dt=1/60, seeded per-vertex N(0, 0.05) forces.
+
+    force_reading="area": sigma is a pressure in N/m^2 times one grid cell of area per
+    vertex (about 0.5 m/s^2 on these vertices); "literal": sigma in newtons per vertex
+    (about 480 m/s^2 of random shaking).
+    """
+    N = 32
+    sigma = force_sigma * (1.0 / (N - 1)) ** 2 if force_reading == "area" else force_sigma
+    F = gaussian_forces(N * N, steps, sigma, seed=0)
+    return Workload(f"grid32_fp32_{steps}steps", [_sheet(N, "top", BASE_MATERIAL, F)], 1.0 / 60.0, steps, "f32",
+                    1e-6)
+
+
+def sample_material(rng):
+    Y = math.exp(rng.uniform(math.log(1e2), math.log(1e4)))
+    kb = math.exp(rng.uniform(math.log(1e-5), math.log(1e-3)))
+    rho = rng.uniform(0.05, 0.5)
+    return np.array([Y, 0.3, kb, rho])
+
+
+def config3(steps=300, N=100):
+    """100x100 grid, two top corners pinned, 300 steps dt=1/30, smooth wind, pinhole loss."""
+    dt = 1.0 / 30.0
+    rest, _ = grid_mesh(N)
+    F = sinusoid_wind(rest, steps, dt, 0.1, (1.0 / (N - 1)) ** 2, seed=0)
+    start = np.array([1e3, 0.3, 1e-4, 0.1])
+    return Workload(f"grid{N}_pinhole_{steps}steps", [_sheet(N, "top2", start, F)], dt, steps, "f32", 1e-6,
+                    checkpoint_every=30, loss="pinhole")
+
+
+def config3_truth():
+    """Ground-truth material of the pinhole workload, drawn with seed 1 from the batch ranges."""
+    return sample_material(np.random.Generator(np.random.PCG64(1)))
+
+
+def config4(count=256, steps=100, nmin=16, nmax=64, seed=1):
+    """Batch of `count` sheets, side N ~ U{nmin..nmax}, materials sampled, two top corners pinned."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sheets = []
+    for _ in range(count):
+        N = int(rng.integers(nmin, nmax + 1))
+        sheets.append(_sheet(N, "top2", sample_material(rng)))
+    return Workload(f"batch{count}_grid{nmin}-{nmax}_{steps}steps", sheets, 1.0 / 30.0, steps, "f32", 1e-6)
+
+
+def config5(steps=200, N=256):
+    """256x256 grid, four corners pinned, 200 steps dt=1/60, smooth wind, checkpoint every 20."""
+    dt = 1.0 / 60.0
+    rest, _ = grid_mesh(N)
+    F = sinusoid_wind(rest, steps, dt, 0.1, (1.0 / (N - 1)) ** 2, seed=0)
+    return Workload(f"grid{N}_corners_{steps}steps", [_sheet(N, "corners", BASE_MATERIAL, F)], dt, steps, "f32",
+                    1e-6, checkpoint_every=20)
+
+
+def grid_counts(N):
+    """(vertices, triangles, interior edges) of an N x N grid."""
+    return N * N, 2 * (N - 1) ** 2, 2 * N * (N - 1) + (N - 1) ** 2 - 4 * (N - 1)
