@@ -1,0 +1,184 @@
+/*
+ * cloth_sim.h - C ABI of the GB300 cloth simulator step and its adjoint.
+ *
+ * The library implements the differentiable physics simulator PS of phi-SfT
+ * (Kairanda et al., CVPR 2022), Sec. 3.1 "Deformation Model":
+ *   S_t = PS(S_{t-1}; phi_{t-1})                                       (Eq. 1)
+ *   phi = {d, S, B, w, F}: density, stretching, bending, wind, per-step
+ *         per-vertex corrective forces                                  (Eq. 2)
+ *   d^2x/dt^2 = M^{-1} f(x, v), M lumped from density and area          (Eq. 3)
+ *   implicit backward Euler, linearised:                                (Eq. 4-5)
+ *       (M - h^2 K) dv = h (f + h K v),   v' = v + dv,   x' = x + h v'
+ * and the gradient of a trajectory loss with respect to the material, the
+ * per-step forces and the initial state by implicit differentiation of every
+ * linear solve (Sec. 3.1, backward pass).  The paper leaves the elastic
+ * energies open; this library uses an isotropic St. Venant-Kirchhoff membrane
+ * on the Green strain (stretch stiffness Y [N/m], Poisson ratio nu) and a
+ * dihedral-angle bending energy 1/2 k_b w_e (theta - theta_rest)^2 per interior
+ * edge with w_e = 3 |e|^2 / (A_1 + A_2).  df/dv = 0 (no damping or drag).
+ *
+ * Conventions for every entry point:
+ *   - Return value: CLOTH_OK (0) or a negative CLOTH_ERR_* code; on error a
+ *     thread-local message is available from cloth_last_error().
+ *   - "device" pointers are CUDA device (or managed) memory owned by the
+ *     caller; the library never frees them.  "host" pointers are read during
+ *     the call only.  The library owns only its handles and the workspace it
+ *     allocates at cloth_batch_create (size: cloth_batch_info).
+ *   - Floating-point device buffers have the batch precision: float for
+ *     CLOTH_FP32, double for CLOTH_FP64.
+ *   - Per-vertex arrays use the packed USER layout: the vertices of sheet 0,
+ *     then sheet 1, ..., each vertex 3 consecutive values (x, y, z):
+ *     [N_total][3].  Trajectories and forces stack steps in front:
+ *     [steps + 1][N_total][3] and [steps][N_total][3].
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous with respect to the host unless stated otherwise.
+ *   - Pinned vertices keep dv = 0 (kinematic pins): their velocity never
+ *     changes, so with v0 = 0 they stay at x0.
+ */
+#ifndef CLOTH_SIM_H
+#define CLOTH_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define CLOTH_OK 0
+#define CLOTH_ERR_INVALID_ARG (-1)    /* null pointer, bad size, bad option       */
+#define CLOTH_ERR_NONMANIFOLD (-2)    /* edge in > 2 triangles or bad winding      */
+#define CLOTH_ERR_DEGENERATE (-3)     /* zero-area rest triangle                   */
+#define CLOTH_ERR_CUDA (-4)           /* a CUDA runtime call failed                */
+#define CLOTH_ERR_OOM (-5)            /* workspace allocation failed               */
+#define CLOTH_ERR_STATE (-6)          /* backward without a matching forward       */
+
+/* ---- per-sheet status bits (device int32 per sheet, OR-ed over a call) ---- */
+#define CLOTH_STATUS_CG_MAXITER 1     /* a solve stopped at cg_max_iter            */
+#define CLOTH_STATUS_INDEFINITE 2     /* p^T A p <= 0 met inside CG                */
+#define CLOTH_STATUS_NONFINITE 4      /* NaN/Inf in a CG scalar                    */
+
+/* ---- options ---- */
+#define CLOTH_FP32 0
+#define CLOTH_FP64 1
+
+#define CLOTH_EXEC_PLAIN 0       /* host-driven CG loop, convergence polled per chunk */
+#define CLOTH_EXEC_GRAPH 1       /* whole trajectory in one CUDA graph; CG loops are
+                                    device-driven conditional WHILE nodes           */
+
+typedef struct cloth_opts {
+  int32_t precision;        /* CLOTH_FP32 or CLOTH_FP64                               */
+  int32_t steps;            /* T >= 1 time steps per trajectory                       */
+  double dt;                /* h > 0 [s]                                              */
+  double cg_tol;            /* CG stops when |r|_2 <= cg_tol |b|_2 (per sheet)        */
+  int32_t cg_max_iter;      /* >= 1                                                   */
+  int32_t checkpoint_every; /* C: velocities and positions kept every C steps; the
+                               backward recomputes each segment. 0 or >= steps: keep
+                               the whole trajectory, no recompute                   */
+  double gravity[3];        /* [m/s^2], e.g. {0, 0, -9.8}                             */
+  double clamp_eta;         /* membrane geometric stiffness in the matrix uses the
+                               smooth positive stress (S + (S^2 + (eta Y)^2 I)^1/2)/2;
+                               0 = exact Hessian (may be indefinite)                 */
+  int32_t exec;             /* CLOTH_EXEC_*                                           */
+  int32_t cg_poll_every;    /* PLAIN mode: CG iterations between host polls (>= 1)    */
+} cloth_opts;
+
+/* Fill `opts` with defaults: FP32, 1 step, dt 1/30, tol 1e-6, 2000 iterations,
+ * no checkpointing, gravity (0, 0, -9.8), clamp_eta 1e-3, GRAPH execution, poll 16. */
+void cloth_default_opts(cloth_opts* opts);
+
+typedef struct cloth_mesh cloth_mesh;
+typedef struct cloth_batch cloth_batch;
+
+/* Create a sheet from its rest (template) mesh S_1 (Sec. 3.1, "fixed topology").
+ * rest_xyz: host [n][3] double, rest positions [m]; tris: host [m][3] int32,
+ * consistently wound triangles; pinned: host [n] uint8 (nonzero = pinned) or NULL.
+ * Errors: INVALID_ARG (n < 3, m < 1, index out of range), DEGENERATE (zero-area
+ * rest triangle), NONMANIFOLD (edge shared by > 2 triangles or opposite winding). */
+int cloth_mesh_create(const double* rest_xyz, int32_t n, const int32_t* tris, int32_t m,
+                      const uint8_t* pinned, cloth_mesh** out);
+int cloth_mesh_destroy(cloth_mesh* mesh);
+/* Vertex, triangle and interior-edge (hinge) counts. */
+int cloth_mesh_info(const cloth_mesh* mesh, int32_t* n, int32_t* m, int32_t* hinges);
+
+/* Create a batch of `count` sheets sharing `opts` and allocate its device
+ * workspace on the current CUDA device (the meshes are copied; they may be
+ * destroyed afterwards).  Sheets may differ in size and material. */
+int cloth_batch_create(const cloth_mesh* const* meshes, int32_t count, const cloth_opts* opts,
+                       cloth_batch** out);
+int cloth_batch_destroy(cloth_batch* batch);
+/* total_vertices = N_total; workspace_bytes = device memory owned by the handle. */
+int cloth_batch_info(const cloth_batch* batch, int32_t* total_vertices, int32_t* count,
+                     size_t* workspace_bytes);
+
+/* Forward trajectory (Eq. 1, Eq. 3-5), all sheets at once.
+ * material: device [count][4] = (Y [N/m], nu, k_b [N m], rho [kg/m^2]) per sheet;
+ * x0, v0: device [N_total][3]; forces: device [steps][N_total][3] newtons, or NULL
+ * for none; traj_x: device [steps + 1][N_total][3], written (traj_x[0] = x0);
+ * status: device [count] int32, written with CLOTH_STATUS_* bits.
+ * Keeps internally what cloth_backward needs (checkpoints). */
+int cloth_forward(cloth_batch* batch, const void* material, const void* x0, const void* v0,
+                  const void* forces, void* traj_x, int32_t* status, void* stream);
+
+/* Adjoint of the last cloth_forward on this handle (same inputs assumed).
+ * dL_dx: device [steps + 1][N_total][3], gradient of the loss w.r.t. every x_t.
+ * Outputs (each may be NULL): g_material [count][4] (dL/dY, 0 for nu, dL/dk_b,
+ * dL/drho), g_forces [steps][N_total][3], g_x0 [N_total][3], g_v0 [N_total][3].
+ * status as in cloth_forward (adjoint solves).  Error STATE if no forward ran. */
+int cloth_backward(cloth_batch* batch, const void* dL_dx, void* g_material, void* g_forces,
+                   void* g_x0, void* g_v0, int32_t* status, void* stream);
+
+/* Trajectory loss L_s = sum_{t=1..steps} sum_{i in s} |x_t^i - target_t^i|^2 per
+ * sheet (a 3-D surrogate of the image energy of Eq. 7-8, accumulated in double).
+ * traj_x, target: device [steps + 1][N_total][3]; loss: device [count] double;
+ * dL_dx: device [steps + 1][N_total][3] or NULL (row t = 0 is written as 0). */
+int cloth_loss_l2(cloth_batch* batch, const void* traj_x, const void* target, double* loss,
+                  void* dL_dx, void* stream);
+
+/* Pinhole reprojection loss per sheet, sum_{t>=1} sum_i |pi(x_t^i) - uv_t^i|^2,
+ * with camera (host double[4]) = (f [px], cx, cy, cz): camera centre c looking
+ * along -z, pi(x) = f ((x - cx) / (cz - z), -(y - cy) / (cz - z)).
+ * target_uv: device [steps + 1][N_total][2]; loss, dL_dx as in cloth_loss_l2.
+ * A point with cz - z <= 0 makes its sheet's loss NaN. */
+int cloth_loss_pinhole(cloth_batch* batch, const void* traj_x, const void* target_uv,
+                       const double* camera, double* loss, void* dL_dx, void* stream);
+
+/* CG iteration totals of the last forward and backward (summed over sheets and
+ * steps; the backward's count includes its recomputed forward solves).
+ * Synchronises the stream of the last call. Any pointer may be NULL. */
+int cloth_stats(cloth_batch* batch, int64_t* fwd_cg_iters, int64_t* bwd_cg_iters,
+                int64_t* recompute_cg_iters);
+
+/* ---- single-kernel entry points (parity checks of each stage) ---- */
+
+/* Internal elastic forces f = -dE/dx at positions x (device [N_total][3]):
+ * f_membrane and f_bending device [N_total][3] (either may be NULL). */
+int cloth_internal_forces(cloth_batch* batch, const void* material, const void* x,
+                          void* f_membrane, void* f_bending, void* stream);
+
+/* The linear system of one step (Eq. 4-5) at state (x, v) with external force
+ * F (device [N_total][3] or NULL), assembled by the step kernels and expanded to
+ * dense per sheet: A: device [sum_s (3 n_s)^2] (sheet blocks one after another,
+ * row-major, user vertex order), b: device [N_total][3].  Pinned rows and
+ * columns are identity, b = 0 there.  For small sheets (testing). */
+int cloth_system_dense(cloth_batch* batch, const void* material, const void* x, const void* v,
+                       const void* F, void* A, void* b, void* stream);
+
+/* y = A p with the assembled system at (x, v) (the CG's SpMV kernel).
+ * p, y: device [N_total][3]. */
+int cloth_spmv(cloth_batch* batch, const void* material, const void* x, const void* v,
+               const void* p, void* y, void* stream);
+
+/* D^3E(x)[a, b, .] for the matrix Hessian (clamped membrane + bending), the
+ * third-derivative contraction of the adjoint: out device [N_total][3]. */
+int cloth_third_contraction(cloth_batch* batch, const void* material, const void* x,
+                            const void* a, const void* b, void* out, void* stream);
+
+/* Thread-local description of the last error (empty string if none). */
+const char* cloth_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLOTH_SIM_H */

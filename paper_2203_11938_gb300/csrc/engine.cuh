@@ -1,0 +1,794 @@
+// Cloth step + adjoint engine: CUDA kernels and host driver, templated on the real type.
+//
+// One time step (phi-SfT Sec. 3.1, Eq. 3-5, df/dv = 0):
+//   element kernels   f_e, H~_e per triangle (membrane) and per interior edge (bending)
+//   assembly          A = M + h^2 H~ (3x3-block SELL-32, pinned rows/cols -> identity),
+//                     b = h (f + M g + F_t) - h^2 H~ v, D^{-1} = 1/diag(A); each block sums a
+//                     fixed list of element blocks (no atomics, fixed order)
+//   Jacobi PCG        per-sheet FP64 dot products by deterministic segmented reduction
+//   update            v' = v + dv, x' = x + h v'
+// Adjoint of step t (implicit differentiation of the solve):
+//   A lam = mask(v_bar + h x_bar);  x_bar += -h H lam - h^2 d(lam^T H~ u)/dx + dL/dx_t,
+//   v_bar += h x_bar - h^2 H~ lam,  F_bar_t = h lam,  with u = v_{t+1};
+//   Y_bar += lam^T (h f_mem - h^2 H~_mem u) / Y, kb_bar likewise, rho_bar += lam^T M_1 (h g - dv).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "elements.cuh"
+#include "engine.h"
+
+namespace cloth {
+
+constexpr int kThreads = kRowsPerBlock;  // row kernels: one CTA per work entry
+constexpr int kElemThreads = 128;
+
+struct CGSheet {
+  double rz, rr, bb, pAp, alpha, beta;
+  int iters, done, status, pad;
+};
+
+enum Phase { kPhaseForward = 0, kPhaseBackward = 1, kPhaseRecompute = 2 };
+
+template <class R>
+struct Dev {
+  int S, Np, Nu, M, E, nslices, NW;
+  const int *tri_v, *tri_sheet;
+  const R* tri_rest;
+  const int *hin_v, *hin_sheet;
+  const R* hin_rest;
+  const int *i2u, *u2i;
+  const uint8_t* pinned;
+  const R* area3;
+  const int *vsheet, *usheet;
+  const int *slice_base, *slice_K, *cols, *contrib_ptr, *contrib;
+  const int *vf_ptr, *vf;
+  const int *work_sheet, *work_row0, *work_rows, *sheet_wfirst;
+  const int *sheet_uoff, *sheet_voff, *sheet_toff, *sheet_hoff;
+  // scratch
+  R *tri_f, *tri_H, *hin_f, *hin_H, *tri_r, *hin_r;
+  double *tri_sc, *hin_sc, *row_sc;
+  R *Aval, *bvec, *dinv, *r, *p, *Ap, *dv;
+  CGSheet* cg;
+  int* cnt;
+  double* part;
+  int* active;
+  unsigned long long* iter_total;
+  double* gacc;  // [S][3] dL/dY, dL/dkb, dL/drho
+  // parameters
+  R h, gx, gy, gz, eta;
+  double tol;
+  int maxit;
+  bool clamp;
+  const R* material;  // [S][4]
+};
+
+// ------------------------------------------------------------------ helpers
+template <class R> __device__ __forceinline__ V3<R> ld3(const R* a, int i) {
+  return {a[3 * (size_t)i], a[3 * (size_t)i + 1], a[3 * (size_t)i + 2]};
+}
+template <class R> __device__ __forceinline__ void st3(R* a, int i, V3<R> v) {
+  a[3 * (size_t)i] = v.x;
+  a[3 * (size_t)i + 1] = v.y;
+  a[3 * (size_t)i + 2] = v.z;
+}
+template <class R> __device__ __forceinline__ V3<R> add3(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> __device__ __forceinline__ V3<R> axpy3(R s, V3<R> x, V3<R> y) {
+  return {s * x.x + y.x, s * x.y + y.y, s * x.z + y.z};
+}
+template <class R> __device__ __forceinline__ double ddot3(V3<R> a, V3<R> b) {
+  return (double)a.x * (double)b.x + (double)a.y * (double)b.y + (double)a.z * (double)b.z;
+}
+
+// Block sum of NV doubles (blockDim.x == kThreads); result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < kThreads / 32 ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Segmented reduction over the work entries of sheet s.  Every CTA of the sheet calls
+// this once; the last CTA to arrive sums all partials in entry order (deterministic)
+// and returns true with the totals in thread 0's `tot`.  No CTA waits for another.
+template <int NV>
+__device__ bool sheet_reduce(double (&v)[NV], int w, int s, const int* wfirst, double* part, int* cnt,
+                             double (&tot)[NV]) {
+  __shared__ int is_last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[(size_t)w * NV + k] = v[k];
+    __threadfence();
+    const int nb = wfirst[s + 1] - wfirst[s];
+    is_last = (atomicAdd(&cnt[s], 1) == nb - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const int w0 = wfirst[s], nb = wfirst[s + 1] - w0;
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int e = threadIdx.x; e < nb; e += kThreads) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&part[(size_t)(w0 + e) * NV + k]);
+  }
+  block_sum<NV>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
+    cnt[s] = 0;
+  }
+  return true;
+}
+
+template <class R>
+__device__ __forceinline__ void finish_sheet(const Dev<R>& d, int s, int phase, cudaGraphConditionalHandle cond,
+                                             int use_cond) {
+  d.cg[s].done = 1;
+  atomicAdd(&d.iter_total[phase], (unsigned long long)d.cg[s].iters);
+  const int left = atomicSub(d.active, 1) - 1;
+  if (left == 0 && use_cond) cudaGraphSetConditional(cond, 0);
+}
+
+// ------------------------------------------------------------------ layout moves
+template <class R>
+__global__ void k_gather(Dev<R> d, const R* __restrict__ in, R* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const int u = d.i2u[i];
+  st3(out, i, u >= 0 && in ? ld3(in, u) : V3<R>{R(0), R(0), R(0)});
+}
+
+template <class R>
+__global__ void k_scatter(Dev<R> d, const R* __restrict__ in, R* __restrict__ out, R s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const int u = d.i2u[i];
+  if (u < 0) return;
+  V3<R> v = ld3(in, i);
+  st3(out, u, V3<R>{s * v.x, s * v.y, s * v.z});
+}
+
+// ------------------------------------------------------------------ element kernels
+template <class R>
+__device__ __forceinline__ TriConst<R> tri_const(const Dev<R>& d, int t) {
+  TriConst<R> k;
+  const int s = d.tri_sheet[t];
+  const R b00 = d.tri_rest[t], b01 = d.tri_rest[(size_t)d.M + t];
+  const R b10 = d.tri_rest[2 * (size_t)d.M + t], b11 = d.tri_rest[3 * (size_t)d.M + t];
+  k.g[1][0] = b00;
+  k.g[1][1] = b01;
+  k.g[2][0] = b10;
+  k.g[2][1] = b11;
+  k.g[0][0] = -(b00 + b10);
+  k.g[0][1] = -(b01 + b11);
+  k.A0 = d.tri_rest[4 * (size_t)d.M + t];
+  const R Y = d.material[4 * s], nu = d.material[4 * s + 1];
+  k.mu = Y / (R(2) * (R(1) + nu));
+  k.lam = Y * nu / (R(1) - nu * nu);
+  k.eps = d.eta * Y;
+  return k;
+}
+
+template <class R>
+__device__ __forceinline__ HingeConst<R> hinge_const(const Dev<R>& d, int e) {
+  const int s = d.hin_sheet[e];
+  return {d.material[4 * s + 2] * d.hin_rest[e], d.hin_rest[(size_t)d.E + e]};
+}
+
+template <class R>
+__global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const R* __restrict__ x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.M) return;
+  TriConst<R> k = tri_const(d, t);
+  V3<R> xe[3], f[3];
+  R H[6][9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) xe[a] = ld3(x, d.tri_v[(size_t)a * d.M + t]);
+  membrane_force_hessian(k, xe, d.clamp, f, H);
+  R* fo = d.tri_f + 9 * (size_t)t;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fo[3 * a] = f[a].x;
+    fo[3 * a + 1] = f[a].y;
+    fo[3 * a + 2] = f[a].z;
+  }
+  R* ho = d.tri_H + 54 * (size_t)t;
+#pragma unroll
+  for (int b = 0; b < 6; ++b)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ho[9 * b + q] = H[b][q];
+}
+
+template <class R>
+__global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const R* __restrict__ x) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
+  HingeConst<R> k = hinge_const(d, e);
+  V3<R> xe[4], f[4];
+  R H[10][9];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) xe[a] = ld3(x, d.hin_v[(size_t)a * d.E + e]);
+  bending_force_hessian(k, xe, f, H);
+  R* fo = d.hin_f + 12 * (size_t)e;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    fo[3 * a] = f[a].x;
+    fo[3 * a + 1] = f[a].y;
+    fo[3 * a + 2] = f[a].z;
+  }
+  R* ho = d.hin_H + 90 * (size_t)e;
+#pragma unroll
+  for (int b = 0; b < 10; ++b)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ho[9 * b + q] = H[b][q];
+}
+
+// element-vertex force slot -> pointer to 3 reals
+template <class R>
+__device__ __forceinline__ const R* force_slot(const Dev<R>& d, int slot) {
+  return slot < 3 * d.M ? d.tri_f + 3 * (size_t)slot : d.hin_f + 3 * (size_t)(slot - 3 * d.M);
+}
+
+// Sum of the element Hessian blocks of SELL entry `ent` (fixed order, transposes applied).
+template <class R>
+__device__ __forceinline__ void gather_block(const Dev<R>& d, int ent, R (&Hb)[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Hb[q] = R(0);
+  const int q0 = d.contrib_ptr[ent], q1 = d.contrib_ptr[ent + 1];
+  for (int q = q0; q < q1; ++q) {
+    const int code = d.contrib[q];
+    const int blk = code >> 1;
+    const R* src = blk < 6 * d.M ? d.tri_H + 9 * (size_t)blk : d.hin_H + 9 * (size_t)(blk - 6 * d.M);
+    if (code & 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) Hb[3 * c + e] += src[3 * e + c];
+    } else {
+#pragma unroll
+      for (int q2 = 0; q2 < 9; ++q2) Hb[q2] += src[q2];
+    }
+  }
+}
+
+// Assembly of A, b, D^{-1} (one thread per row; a warp is one SELL slice).
+// Fext: user-layout external force of this step or null.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __restrict__ v, const R* __restrict__ Fext) {
+  const int w = blockIdx.x;
+  const int s = d.work_sheet[w];
+  if (threadIdx.x >= d.work_rows[w]) return;
+  const int i = d.work_row0[w] + threadIdx.x;
+  const int sl = i >> 5, lane = i & 31;
+  const int K = d.slice_K[sl], base = d.slice_base[sl];
+  const bool pin_i = d.pinned[i] != 0;
+  const R rho = d.material[4 * s + 3];
+  const R mass = rho * d.area3[i];
+  const R h = d.h, h2 = d.h * d.h;
+  V3<R> f = {R(0), R(0), R(0)};
+  for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
+    const R* src = force_slot(d, d.vf[q]);
+    f.x += src[0];
+    f.y += src[1];
+    f.z += src[2];
+  }
+  V3<R> Hv = {R(0), R(0), R(0)};
+  R diag[3] = {R(1), R(1), R(1)};
+  for (int k = 0; k < K; ++k) {
+    const int ent = (base + k) * 32 + lane;
+    const int j = d.cols[ent];
+    R Hb[9];
+    gather_block(d, ent, Hb);
+    const V3<R> vj = ld3(v, j);
+    Hv.x += Hb[0] * vj.x + Hb[1] * vj.y + Hb[2] * vj.z;
+    Hv.y += Hb[3] * vj.x + Hb[4] * vj.y + Hb[5] * vj.z;
+    Hv.z += Hb[6] * vj.x + Hb[7] * vj.y + Hb[8] * vj.z;
+    const bool zero = pin_i || d.pinned[j] != 0;
+    R* dst = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      R a = zero ? R(0) : h2 * Hb[q];
+      if (k == 0 && (q == 0 || q == 4 || q == 8)) {
+        a += pin_i ? R(1) : mass;
+        diag[q / 4] = a;
+      }
+      dst[q * 32] = a;
+    }
+  }
+  V3<R> b = {R(0), R(0), R(0)};
+  if (!pin_i) {
+    const int u = d.i2u[i];
+    V3<R> fe = Fext && u >= 0 ? ld3(Fext, u) : V3<R>{R(0), R(0), R(0)};
+    b.x = h * (f.x + mass * d.gx + fe.x) - h2 * Hv.x;
+    b.y = h * (f.y + mass * d.gy + fe.y) - h2 * Hv.y;
+    b.z = h * (f.z + mass * d.gz + fe.z) - h2 * Hv.z;
+  }
+  st3(d.bvec, i, b);
+  st3(d.dinv, i, V3<R>{R(1) / diag[0], R(1) / diag[1], R(1) / diag[2]});
+}
+
+// ------------------------------------------------------------------ CG
+template <class R>
+__global__ void k_solve_begin(Dev<R> d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *d.active = d.S;
+}
+
+template <class R>
+__global__ void k_cond_set(Dev<R> d, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, *d.active > 0 ? 1u : 0u);
+}
+
+// r = rhs, dv = 0, p = z = D^{-1} r; rz, rr, bb per sheet.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restrict__ rhs, int phase) {
+  const int w = blockIdx.x, s = d.work_sheet[w];
+  const bool on = threadIdx.x < d.work_rows[w];
+  const int i = d.work_row0[w] + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (on) {
+    const V3<R> r = ld3(rhs, i);
+    const V3<R> di = ld3(d.dinv, i);
+    const V3<R> z = {di.x * r.x, di.y * r.y, di.z * r.z};
+    st3(d.r, i, r);
+    st3(d.p, i, z);
+    st3(d.dv, i, V3<R>{R(0), R(0), R(0)});
+    v[0] = ddot3(r, z);
+    v[1] = ddot3(r, r);
+  }
+  double tot[2];
+  if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
+    CGSheet& c = d.cg[s];
+    c.rz = tot[0];
+    c.rr = tot[1];
+    c.bb = tot[1];
+    c.iters = 0;
+    c.done = 0;
+    bool fin = false;
+    if (!isfinite(tot[1])) {
+      c.status |= CLOTH_STATUS_NONFINITE;
+      fin = true;
+    } else if (tot[1] == 0.0 || sqrt(tot[1]) <= d.tol * sqrt(tot[1])) {
+      fin = true;
+    }
+    if (fin) finish_sheet(d, s, phase, 0, 0);
+  }
+}
+
+// Ap = A p (SELL-32 3x3 blocks), pAp per sheet, alpha = rz / pAp.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
+                                                      int use_cond) {
+  const int w = blockIdx.x, s = d.work_sheet[w];
+  if (d.cg[s].done) return;
+  const bool on = threadIdx.x < d.work_rows[w];
+  const int i = d.work_row0[w] + threadIdx.x;
+  double v[1] = {0.0};
+  if (on) {
+    const int sl = i >> 5, lane = i & 31;
+    const int K = d.slice_K[sl], base = d.slice_base[sl];
+    V3<R> y = {R(0), R(0), R(0)};
+    for (int k = 0; k < K; ++k) {
+      const int ent = (base + k) * 32 + lane;
+      const int j = d.cols[ent];
+      const R* a = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
+      const V3<R> pj = ld3(d.p, j);
+      y.x += a[0] * pj.x + a[32] * pj.y + a[64] * pj.z;
+      y.y += a[96] * pj.x + a[128] * pj.y + a[160] * pj.z;
+      y.z += a[192] * pj.x + a[224] * pj.y + a[256] * pj.z;
+    }
+    st3(d.Ap, i, y);
+    v[0] = ddot3(ld3(d.p, i), y);
+  }
+  double tot[1];
+  if (sheet_reduce<1>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
+    CGSheet& c = d.cg[s];
+    c.pAp = tot[0];
+    if (!isfinite(tot[0])) {
+      c.status |= CLOTH_STATUS_NONFINITE;
+      finish_sheet(d, s, phase, cond, use_cond);
+    } else if (tot[0] <= 0.0) {
+      c.status |= CLOTH_STATUS_INDEFINITE;
+      finish_sheet(d, s, phase, cond, use_cond);
+    } else {
+      c.alpha = c.rz / tot[0];
+    }
+  }
+}
+
+// dv += alpha p, r -= alpha Ap, z = D^{-1} r; rz, rr; beta; convergence.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
+                                                        int use_cond) {
+  const int w = blockIdx.x, s = d.work_sheet[w];
+  if (d.cg[s].done) return;
+  const bool on = threadIdx.x < d.work_rows[w];
+  const int i = d.work_row0[w] + threadIdx.x;
+  const R alpha = (R)d.cg[s].alpha;
+  double v[2] = {0.0, 0.0};
+  if (on) {
+    const V3<R> p = ld3(d.p, i), Ap = ld3(d.Ap, i);
+    V3<R> x = ld3(d.dv, i), r = ld3(d.r, i);
+    x = axpy3(alpha, p, x);
+    r = axpy3(-alpha, Ap, r);
+    st3(d.dv, i, x);
+    st3(d.r, i, r);
+    const V3<R> di = ld3(d.dinv, i);
+    const V3<R> z = {di.x * r.x, di.y * r.y, di.z * r.z};
+    v[0] = ddot3(r, z);
+    v[1] = ddot3(r, r);
+  }
+  double tot[2];
+  if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
+    CGSheet& c = d.cg[s];
+    c.beta = tot[0] / c.rz;
+    c.rz = tot[0];
+    c.rr = tot[1];
+    c.iters += 1;
+    if (!isfinite(tot[1]) || !isfinite(tot[0])) {
+      c.status |= CLOTH_STATUS_NONFINITE;
+      finish_sheet(d, s, phase, cond, use_cond);
+    } else if (sqrt(tot[1]) <= d.tol * sqrt(c.bb)) {
+      finish_sheet(d, s, phase, cond, use_cond);
+    } else if (c.iters >= d.maxit) {
+      c.status |= CLOTH_STATUS_CG_MAXITER;
+      finish_sheet(d, s, phase, cond, use_cond);
+    }
+  }
+}
+
+// p = D^{-1} r + beta p
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
+  const int w = blockIdx.x, s = d.work_sheet[w];
+  if (d.cg[s].done) return;
+  if (threadIdx.x >= d.work_rows[w]) return;
+  const int i = d.work_row0[w] + threadIdx.x;
+  const R beta = (R)d.cg[s].beta;
+  const V3<R> r = ld3(d.r, i), di = ld3(d.dinv, i), p = ld3(d.p, i);
+  st3(d.p, i, V3<R>{di.x * r.x + beta * p.x, di.y * r.y + beta * p.y, di.z * r.z + beta * p.z});
+}
+
+// v' = v + dv, x' = x + h v'; optional user-layout copy of x'.
+template <class R>
+__global__ void k_state_update(Dev<R> d, const R* __restrict__ x, const R* __restrict__ v, R* __restrict__ xn,
+                               R* __restrict__ vn, R* __restrict__ traj_row) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const V3<R> dv = ld3(d.dv, i);
+  const V3<R> v1 = add3(ld3(v, i), dv);
+  const V3<R> x1 = axpy3(d.h, v1, ld3(x, i));
+  st3(vn, i, v1);
+  st3(xn, i, x1);
+  const int u = d.i2u[i];
+  if (traj_row && u >= 0) st3(traj_row, u, x1);
+}
+
+template <class R>
+__global__ void k_reset_status(Dev<R> d, int phase) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < d.S) d.cg[s].status = 0;
+  if (s == 0) d.iter_total[phase] = 0;
+}
+
+template <class R>
+__global__ void k_status_out(Dev<R> d, int32_t* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < d.S) status[s] = d.cg[s].status;
+}
+
+// ------------------------------------------------------------------ adjoint kernels
+// mode 0: adjoint step contributions; mode 1: third-derivative contraction only.
+template <class R>
+__global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const R* __restrict__ x,
+                                                         const R* __restrict__ lam, const R* __restrict__ u, int mode) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.M) return;
+  TriConst<R> k = tri_const(d, t);
+  V3<R> xe[3], le[3], ue[3], f[3], Hx[3], Hl[3], Hu[3], th[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int vi = d.tri_v[(size_t)a * d.M + t];
+    xe[a] = ld3(x, vi);
+    le[a] = ld3(lam, vi);
+    ue[a] = ld3(u, vi);
+  }
+  membrane_adjoint(k, xe, le, ue, d.clamp, f, Hx, Hl, Hu, th);
+  const R h = d.h, h2 = d.h * d.h;
+  R* ro = d.tri_r + 18 * (size_t)t;
+  double sc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (mode == 0) {
+      ro[6 * a + 0] = -h * Hx[a].x - h2 * th[a].x;
+      ro[6 * a + 1] = -h * Hx[a].y - h2 * th[a].y;
+      ro[6 * a + 2] = -h * Hx[a].z - h2 * th[a].z;
+      ro[6 * a + 3] = -h2 * Hl[a].x;
+      ro[6 * a + 4] = -h2 * Hl[a].y;
+      ro[6 * a + 5] = -h2 * Hl[a].z;
+      sc += (double)le[a].x * (double)(h * f[a].x - h2 * Hu[a].x) + (double)le[a].y * (double)(h * f[a].y - h2 * Hu[a].y) +
+            (double)le[a].z * (double)(h * f[a].z - h2 * Hu[a].z);
+    } else {
+      ro[6 * a + 0] = th[a].x;
+      ro[6 * a + 1] = th[a].y;
+      ro[6 * a + 2] = th[a].z;
+      ro[6 * a + 3] = R(0);
+      ro[6 * a + 4] = R(0);
+      ro[6 * a + 5] = R(0);
+    }
+  }
+  const int s = d.tri_sheet[t];
+  d.tri_sc[t] = sc / (double)d.material[4 * s];
+}
+
+template <class R>
+__global__ void __launch_bounds__(kElemThreads) k_adj_hinge(Dev<R> d, const R* __restrict__ x,
+                                                           const R* __restrict__ lam, const R* __restrict__ u, int mode) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
+  HingeConst<R> k = hinge_const(d, e);
+  V3<R> xe[4], le[4], ue[4], f[4], Hl[4], Hu[4], th[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int vi = d.hin_v[(size_t)a * d.E + e];
+    xe[a] = ld3(x, vi);
+    le[a] = ld3(lam, vi);
+    ue[a] = ld3(u, vi);
+  }
+  bending_adjoint(k, xe, le, ue, f, Hl, Hu, th);
+  const R h = d.h, h2 = d.h * d.h;
+  R* ro = d.hin_r + 24 * (size_t)e;
+  double sc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (mode == 0) {
+      ro[6 * a + 0] = -h * Hl[a].x - h2 * th[a].x;
+      ro[6 * a + 1] = -h * Hl[a].y - h2 * th[a].y;
+      ro[6 * a + 2] = -h * Hl[a].z - h2 * th[a].z;
+      ro[6 * a + 3] = -h2 * Hl[a].x;
+      ro[6 * a + 4] = -h2 * Hl[a].y;
+      ro[6 * a + 5] = -h2 * Hl[a].z;
+      sc += (double)le[a].x * (double)(h * f[a].x - h2 * Hu[a].x) + (double)le[a].y * (double)(h * f[a].y - h2 * Hu[a].y) +
+            (double)le[a].z * (double)(h * f[a].z - h2 * Hu[a].z);
+    } else {
+      ro[6 * a + 0] = th[a].x;
+      ro[6 * a + 1] = th[a].y;
+      ro[6 * a + 2] = th[a].z;
+      ro[6 * a + 3] = R(0);
+      ro[6 * a + 4] = R(0);
+      ro[6 * a + 5] = R(0);
+    }
+  }
+  const int s = d.hin_sheet[e];
+  d.hin_sc[e] = sc / (double)d.material[4 * s + 2];
+}
+
+template <class R>
+__device__ __forceinline__ const R* adj_slot(const Dev<R>& d, int slot) {
+  return slot < 3 * d.M ? d.tri_r + 6 * (size_t)slot : d.hin_r + 6 * (size_t)(slot - 3 * d.M);
+}
+
+// RHS of the adjoint solve: mask(v_bar + h x_bar)
+template <class R>
+__global__ void k_adj_rhs(Dev<R> d, const R* __restrict__ ax, const R* __restrict__ av) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  V3<R> g = {R(0), R(0), R(0)};
+  if (!d.pinned[i]) g = axpy3(d.h, ld3(ax, i), ld3(av, i));
+  st3(d.bvec, i, g);
+}
+
+// Per-vertex adjoint update after the element pass; lam = d.dv.
+template <class R>
+__global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, const R* __restrict__ v_t,
+                             const R* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  V3<R> r1 = {R(0), R(0), R(0)}, r2 = {R(0), R(0), R(0)};
+  for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
+    const R* src = adj_slot(d, d.vf[q]);
+    r1.x += src[0];
+    r1.y += src[1];
+    r1.z += src[2];
+    r2.x += src[3];
+    r2.y += src[4];
+    r2.z += src[5];
+  }
+  const int u = d.i2u[i];
+  const V3<R> a_x = ld3(ax, i), a_v = ld3(av, i), lam = ld3(d.dv, i);
+  const V3<R> dl = (dLdx_row && u >= 0) ? ld3(dLdx_row, u) : V3<R>{R(0), R(0), R(0)};
+  st3(ax, i, V3<R>{a_x.x + r1.x + dl.x, a_x.y + r1.y + dl.y, a_x.z + r1.z + dl.z});
+  st3(av, i, V3<R>{a_v.x + d.h * a_x.x + r2.x, a_v.y + d.h * a_x.y + r2.y, a_v.z + d.h * a_x.z + r2.z});
+  if (gF_row && u >= 0) st3(gF_row, u, V3<R>{d.h * lam.x, d.h * lam.y, d.h * lam.z});
+  const V3<R> vt = ld3(v_t, i), vt1 = ld3(v_t1, i);
+  const int s = d.vsheet[i];
+  const double m1 = (double)d.area3[i];
+  d.row_sc[i] = m1 * ((double)lam.x * ((double)d.h * (double)d.gx - ((double)vt1.x - (double)vt.x)) +
+                      (double)lam.y * ((double)d.h * (double)d.gy - ((double)vt1.y - (double)vt.y)) +
+                      (double)lam.z * ((double)d.h * (double)d.gz - ((double)vt1.z - (double)vt.z)));
+  (void)s;
+}
+
+// Per-sheet accumulation of the material gradients (deterministic).
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_param_acc(Dev<R> d) {
+  const int s = blockIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int t = d.sheet_toff[s] + threadIdx.x; t < d.sheet_toff[s + 1]; t += kThreads) v[0] += d.tri_sc[t];
+  for (int e = d.sheet_hoff[s] + threadIdx.x; e < d.sheet_hoff[s + 1]; e += kThreads) v[1] += d.hin_sc[e];
+  for (int i = d.sheet_voff[s] + threadIdx.x; i < d.sheet_voff[s + 1]; i += kThreads) v[2] += d.row_sc[i];
+  block_sum<3>(v);
+  if (threadIdx.x == 0) {
+    d.gacc[3 * s] += v[0];
+    d.gacc[3 * s + 1] += v[1];
+    d.gacc[3 * s + 2] += v[2];
+  }
+}
+
+template <class R>
+__global__ void k_grad_material(Dev<R> d, R* __restrict__ g) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.S) return;
+  g[4 * s] = (R)d.gacc[3 * s];
+  g[4 * s + 1] = R(0);
+  g[4 * s + 2] = (R)d.gacc[3 * s + 1];
+  g[4 * s + 3] = (R)d.gacc[3 * s + 2];
+}
+
+// ------------------------------------------------------------------ test-only kernels
+// per-vertex force of one kind (kind 0 membrane, 1 bending) in user layout
+template <class R>
+__global__ void k_vertex_force(Dev<R> d, int kind, R* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const int u = d.i2u[i];
+  if (u < 0) return;
+  V3<R> f = {R(0), R(0), R(0)};
+  for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
+    const int slot = d.vf[q];
+    if ((slot < 3 * d.M) != (kind == 0)) continue;
+    const R* src = force_slot(d, slot);
+    f = add3(f, V3<R>{src[0], src[1], src[2]});
+  }
+  st3(out, u, f);
+}
+
+template <class R>
+__global__ void k_vertex_third(Dev<R> d, R* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const int u = d.i2u[i];
+  if (u < 0) return;
+  V3<R> f = {R(0), R(0), R(0)};
+  for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
+    const R* src = adj_slot(d, d.vf[q]);
+    f = add3(f, V3<R>{src[0], src[1], src[2]});
+  }
+  st3(out, u, f);
+}
+
+// Expand the SELL matrix of each sheet into a dense row-major block (user order).
+template <class R>
+__global__ void k_dense(Dev<R> d, const long long* __restrict__ dense_off, R* __restrict__ A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const int u = d.i2u[i];
+  if (u < 0) return;
+  const int s = d.vsheet[i];
+  const int n = d.sheet_uoff[s + 1] - d.sheet_uoff[s];
+  const int ul = u - d.sheet_uoff[s];
+  const int sl = i >> 5, lane = i & 31;
+  for (int k = 0; k < d.slice_K[sl]; ++k) {
+    const int ent = (d.slice_base[sl] + k) * 32 + lane;
+    const int j = d.cols[ent];
+    const int uj = d.i2u[j];
+    if (uj < 0) continue;
+    if (k > 0 && j == i) continue;  // padding slot
+    const int ujl = uj - d.sheet_uoff[s];
+    const R* a = d.Aval + (size_t)(d.slice_base[sl] + k) * 32 * 9 + lane;
+    for (int c = 0; c < 3; ++c)
+      for (int e = 0; e < 3; ++e)
+        A[dense_off[s] + (size_t)(3 * ul + c) * (3 * n) + 3 * ujl + e] = a[(3 * c + e) * 32];
+  }
+}
+
+// y = A p outside CG (for the single-kernel entry point)
+template <class R>
+__global__ void k_spmv_plain(Dev<R> d, const R* __restrict__ p, R* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const int sl = i >> 5, lane = i & 31;
+  V3<R> acc = {R(0), R(0), R(0)};
+  for (int k = 0; k < d.slice_K[sl]; ++k) {
+    const int ent = (d.slice_base[sl] + k) * 32 + lane;
+    const R* a = d.Aval + (size_t)(d.slice_base[sl] + k) * 32 * 9 + lane;
+    const V3<R> pj = ld3(p, d.cols[ent]);
+    acc.x += a[0] * pj.x + a[32] * pj.y + a[64] * pj.z;
+    acc.y += a[96] * pj.x + a[128] * pj.y + a[160] * pj.z;
+    acc.z += a[192] * pj.x + a[224] * pj.y + a[256] * pj.z;
+  }
+  st3(y, i, acc);
+}
+
+// ------------------------------------------------------------------ losses
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_loss_l2(Dev<R> d, int T, const R* __restrict__ traj,
+                                                      const R* __restrict__ tgt, R* __restrict__ grad,
+                                                      double* __restrict__ lpart) {
+  const int s = blockIdx.x, t = blockIdx.y + 1;
+  const int u0 = d.sheet_uoff[s], u1 = d.sheet_uoff[s + 1];
+  const size_t row = (size_t)t * d.Nu;
+  double v[1] = {0.0};
+  for (int u = u0 + threadIdx.x; u < u1; u += kThreads) {
+    const V3<R> x = ld3(traj + 3 * row, u), y = ld3(tgt + 3 * row, u);
+    const V3<R> df = {x.x - y.x, x.y - y.y, x.z - y.z};
+    v[0] += ddot3(df, df);
+    if (grad) st3(grad + 3 * row, u, V3<R>{R(2) * df.x, R(2) * df.y, R(2) * df.z});
+  }
+  block_sum<1>(v);
+  if (threadIdx.x == 0) lpart[(size_t)s * T + (t - 1)] = v[0];
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_loss_pinhole(Dev<R> d, int T, const R* __restrict__ traj,
+                                                           const R* __restrict__ uv, double f, double cx, double cy,
+                                                           double cz, R* __restrict__ grad,
+                                                           double* __restrict__ lpart) {
+  const int s = blockIdx.x, t = blockIdx.y + 1;
+  const int u0 = d.sheet_uoff[s], u1 = d.sheet_uoff[s + 1];
+  const size_t row = (size_t)t * d.Nu;
+  double v[1] = {0.0};
+  for (int u = u0 + threadIdx.x; u < u1; u += kThreads) {
+    const V3<R> x = ld3(traj + 3 * row, u);
+    const double Xc = (double)x.x - cx, Yc = -((double)x.y - cy), Zc = cz - (double)x.z;
+    if (!(Zc > 0.0)) {
+      v[0] += NAN;
+      continue;
+    }
+    const double pu = f * Xc / Zc, pv = f * Yc / Zc;
+    const double du = pu - (double)uv[2 * (row + u)], dw = pv - (double)uv[2 * (row + u) + 1];
+    v[0] += du * du + dw * dw;
+    if (grad)
+      st3(grad + 3 * row, u,
+          V3<R>{(R)(2.0 * du * f / Zc), (R)(-2.0 * dw * f / Zc), (R)(2.0 * (du * f * Xc + dw * f * Yc) / (Zc * Zc))});
+  }
+  block_sum<1>(v);
+  if (threadIdx.x == 0) lpart[(size_t)s * T + (t - 1)] = v[0];
+}
+
+template <class R>
+__global__ void k_loss_final(Dev<R> d, int T, const double* __restrict__ lpart, double* __restrict__ loss) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.S) return;
+  double acc = 0.0;
+  for (int t = 0; t < T; ++t) acc += lpart[(size_t)s * T + t];
+  loss[s] = acc;
+}
+
+}  // namespace cloth

@@ -1,0 +1,9 @@
+// FP32 instantiation of the cloth engine (element kernels, SpMV and CG vectors in
+// float; CG dot products, residual norms and gradient reductions in double).
+#include "engine_impl.cuh"
+
+namespace cloth {
+std::unique_ptr<EngineBase> make_engine_f32(const BatchLayout& L, const cloth_opts& o, int* rc, std::string* err) {
+  return make_engine<float>(L, o, rc, err);
+}
+}  // namespace cloth

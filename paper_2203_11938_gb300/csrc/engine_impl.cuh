@@ -1,0 +1,571 @@
+// Host driver of the cloth engine (buffers, trajectory segments, execution modes).
+#pragma once
+
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace cloth {
+
+#define CLOTH_CUDA(expr)                                                                         \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      set_last_error(std::string(#expr) + ": " + cudaGetErrorString(e_));                        \
+      return CLOTH_ERR_CUDA;                                                                     \
+    }                                                                                            \
+  } while (0)
+
+#define CLOTH_TRY(expr)        \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != CLOTH_OK) return rc_; \
+  } while (0)
+
+template <class R>
+class Engine final : public EngineBase {
+ public:
+  Engine(const BatchLayout& L, const cloth_opts& o) : L_(L), o_(o) {}
+
+  ~Engine() override {
+    for (auto& g : graphs_)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (cap_stream_) cudaStreamDestroy(cap_stream_);
+    if (body_stream_) cudaStreamDestroy(body_stream_);
+    if (host_active_) cudaFreeHost(host_active_);
+    for (void* p : allocs_) cudaFree(p);
+  }
+
+  int init(std::string* err) {
+    T_ = o_.steps;
+    C_ = (o_.checkpoint_every >= 1 && o_.checkpoint_every < T_) ? o_.checkpoint_every : T_;
+    nseg_ = (T_ + C_ - 1) / C_;
+    Dev<R>& d = d_;
+    std::memset(&d, 0, sizeof(d));
+    d.S = L_.S;
+    d.Np = L_.Np;
+    d.Nu = L_.Nu;
+    d.M = L_.M;
+    d.E = L_.E;
+    d.nslices = L_.nslices;
+    d.NW = (int)L_.work_sheet.size();
+    d.h = (R)o_.dt;
+    d.gx = (R)o_.gravity[0];
+    d.gy = (R)o_.gravity[1];
+    d.gz = (R)o_.gravity[2];
+    d.eta = (R)o_.clamp_eta;
+    d.clamp = o_.clamp_eta > 0.0;
+    d.tol = o_.cg_tol;
+    d.maxit = o_.cg_max_iter;
+    int rc = CLOTH_OK;
+    auto up_i = [&](const std::vector<int>& v) -> const int* { return upload(v, &rc); };
+    auto up_r = [&](const std::vector<double>& v) -> const R* {
+      std::vector<R> c(v.begin(), v.end());
+      return upload(c, &rc);
+    };
+    d.tri_v = up_i(L_.tri_v);
+    d.tri_sheet = up_i(L_.tri_sheet);
+    d.tri_rest = up_r(L_.tri_rest);
+    d.hin_v = up_i(L_.hin_v);
+    d.hin_sheet = up_i(L_.hin_sheet);
+    d.hin_rest = up_r(L_.hin_rest);
+    d.i2u = up_i(L_.i2u);
+    d.u2i = up_i(L_.u2i);
+    d.pinned = upload(L_.pinned, &rc);
+    d.area3 = up_r(L_.area3);
+    d.vsheet = up_i(L_.vsheet);
+    d.usheet = up_i(L_.usheet);
+    d.slice_base = up_i(L_.slice_base);
+    d.slice_K = up_i(L_.slice_K);
+    d.cols = up_i(L_.cols);
+    d.contrib_ptr = up_i(L_.contrib_ptr);
+    d.contrib = up_i(L_.contrib);
+    d.vf_ptr = up_i(L_.vf_ptr);
+    d.vf = up_i(L_.vf);
+    d.work_sheet = up_i(L_.work_sheet);
+    d.work_row0 = up_i(L_.work_row0);
+    d.work_rows = up_i(L_.work_rows);
+    d.sheet_wfirst = up_i(L_.sheet_wfirst);
+    d.sheet_uoff = up_i(L_.sheet_uoff);
+    d.sheet_voff = up_i(L_.sheet_voff);
+    d.sheet_toff = up_i(L_.sheet_toff);
+    d.sheet_hoff = up_i(L_.sheet_hoff);
+    const size_t n3 = 3 * (size_t)L_.Np;
+    const size_t M = L_.M, E = L_.E;
+    d.tri_f = alloc<R>(9 * M, &rc);
+    d.tri_H = alloc<R>(54 * M, &rc);
+    d.hin_f = alloc<R>(12 * E, &rc);
+    d.hin_H = alloc<R>(90 * E, &rc);
+    d.tri_r = alloc<R>(18 * M, &rc);
+    d.hin_r = alloc<R>(24 * E, &rc);
+    d.tri_sc = alloc<double>(M, &rc);
+    d.hin_sc = alloc<double>(E, &rc);
+    d.row_sc = alloc<double>(L_.Np, &rc);
+    d.Aval = alloc<R>((size_t)L_.total_slots() * 32 * 9, &rc);
+    d.bvec = alloc<R>(n3, &rc);
+    d.dinv = alloc<R>(n3, &rc);
+    d.r = alloc<R>(n3, &rc);
+    d.p = alloc<R>(n3, &rc);
+    d.Ap = alloc<R>(n3, &rc);
+    d.dv = alloc<R>(n3, &rc);
+    d.cg = alloc<CGSheet>(L_.S, &rc);
+    d.cnt = alloc<int>(L_.S, &rc);
+    d.part = alloc<double>(2 * (size_t)d.NW, &rc);
+    d.active = alloc<int>(1, &rc);
+    d.iter_total = alloc<unsigned long long>(3, &rc);
+    d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
+    seg_x_ = alloc<R>(n3 * (C_ + 1), &rc);
+    seg_v_ = alloc<R>(n3 * (C_ + 1), &rc);
+    if (nseg_ > 1) {
+      ck_x_ = alloc<R>(n3 * nseg_, &rc);
+      ck_v_ = alloc<R>(n3 * nseg_, &rc);
+    }
+    ax_ = alloc<R>(n3, &rc);
+    av_ = alloc<R>(n3, &rc);
+    tmp_a_ = alloc<R>(n3, &rc);
+    tmp_b_ = alloc<R>(n3, &rc);
+    tmp_c_ = alloc<R>(n3, &rc);
+    lpart_ = alloc<double>((size_t)L_.S * T_, &rc);
+    if (rc != CLOTH_OK) {
+      *err = "device allocation failed";
+      return rc;
+    }
+    if (cudaMemset(d.cnt, 0, sizeof(int) * L_.S) != cudaSuccess ||
+        cudaMemset(d.cg, 0, sizeof(CGSheet) * L_.S) != cudaSuccess ||
+        cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
+        cudaMallocHost(&host_active_, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&body_stream_, cudaStreamNonBlocking) != cudaSuccess) {
+      *err = "CUDA setup failed";
+      return CLOTH_ERR_CUDA;
+    }
+    return CLOTH_OK;
+  }
+
+  size_t workspace_bytes() const override { return bytes_; }
+  int total_vertices() const override { return L_.Nu; }
+  int count() const override { return L_.S; }
+
+  // ---------------------------------------------------------------- forward
+  int forward(const void* material, const void* x0, const void* v0, const void* forces, void* traj_x,
+              int32_t* status, void* stream_) override {
+    if (!material || !x0 || !v0 || !traj_x || !status) {
+      set_last_error("cloth_forward: material, x0, v0, traj_x and status must be non-null");
+      return CLOTH_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream_;
+    last_stream_ = st;
+    d_.material = (const R*)material;
+    fwd_material_ = material;
+    fwd_forces_ = forces;
+    if (o_.exec == CLOTH_EXEC_GRAPH) {
+      GraphKey key{0, {material, x0, v0, forces, traj_x, status, nullptr, nullptr, nullptr, nullptr}, 0};
+      CLOTH_TRY(run_graph(key, st, [&](cudaStream_t s) {
+        return forward_body(material, x0, v0, forces, traj_x, status, s, true);
+      }));
+    } else {
+      CLOTH_TRY(forward_body(material, x0, v0, forces, traj_x, status, st, false));
+    }
+    have_forward_ = true;
+    seg_valid_ = nseg_ - 1;
+    return CLOTH_OK;
+  }
+
+  int backward(const void* dL_dx, void* g_material, void* g_forces, void* g_x0, void* g_v0, int32_t* status,
+               void* stream_) override {
+    if (!have_forward_) {
+      set_last_error("cloth_backward: no forward pass on this handle");
+      return CLOTH_ERR_STATE;
+    }
+    if (!dL_dx || !status) {
+      set_last_error("cloth_backward: dL_dx and status must be non-null");
+      return CLOTH_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream_;
+    last_stream_ = st;
+    d_.material = (const R*)fwd_material_;
+    const int seg_valid = seg_valid_;
+    if (o_.exec == CLOTH_EXEC_GRAPH) {
+      GraphKey key{1, {fwd_material_, fwd_forces_, dL_dx, g_material, g_forces, g_x0, g_v0, status, nullptr, nullptr},
+                   seg_valid};
+      CLOTH_TRY(run_graph(key, st, [&](cudaStream_t s) {
+        return backward_body(dL_dx, g_material, g_forces, g_x0, g_v0, status, s, true, seg_valid);
+      }));
+    } else {
+      CLOTH_TRY(backward_body(dL_dx, g_material, g_forces, g_x0, g_v0, status, st, false, seg_valid));
+    }
+    seg_valid_ = 0;
+    return CLOTH_OK;
+  }
+
+  int stats(int64_t* fwd, int64_t* bwd, int64_t* rec) override {
+    CLOTH_CUDA(cudaStreamSynchronize(last_stream_));
+    unsigned long long h[3];
+    CLOTH_CUDA(cudaMemcpy(h, d_.iter_total, sizeof(h), cudaMemcpyDeviceToHost));
+    if (fwd) *fwd = (int64_t)h[0];
+    if (bwd) *bwd = (int64_t)h[1];
+    if (rec) *rec = (int64_t)h[2];
+    return CLOTH_OK;
+  }
+
+  // ---------------------------------------------------------------- losses
+  int loss_l2(const void* traj, const void* target, double* loss, void* grad, void* stream_) override {
+    if (!traj || !target || !loss) {
+      set_last_error("cloth_loss_l2: traj, target and loss must be non-null");
+      return CLOTH_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream_;
+    if (grad) CLOTH_CUDA(cudaMemsetAsync(grad, 0, sizeof(R) * 3 * (size_t)L_.Nu, st));
+    dim3 grid(L_.S, T_);
+    k_loss_l2<R><<<grid, kThreads, 0, st>>>(d_, T_, (const R*)traj, (const R*)target, (R*)grad, lpart_);
+    k_loss_final<R><<<(L_.S + 127) / 128, 128, 0, st>>>(d_, T_, lpart_, loss);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  int loss_pinhole(const void* traj, const void* uv, const double* cam, double* loss, void* grad,
+                   void* stream_) override {
+    if (!traj || !uv || !cam || !loss) {
+      set_last_error("cloth_loss_pinhole: traj, target_uv, camera and loss must be non-null");
+      return CLOTH_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream_;
+    if (grad) CLOTH_CUDA(cudaMemsetAsync(grad, 0, sizeof(R) * 3 * (size_t)L_.Nu, st));
+    dim3 grid(L_.S, T_);
+    k_loss_pinhole<R><<<grid, kThreads, 0, st>>>(d_, T_, (const R*)traj, (const R*)uv, cam[0], cam[1], cam[2],
+                                                 cam[3], (R*)grad, lpart_);
+    k_loss_final<R><<<(L_.S + 127) / 128, 128, 0, st>>>(d_, T_, lpart_, loss);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  // ---------------------------------------------------------------- single stages
+  int internal_forces(const void* material, const void* x, void* fm, void* fb, void* stream_) override {
+    if (!material || !x) return invalid("cloth_internal_forces: material and x must be non-null");
+    cudaStream_t st = (cudaStream_t)stream_;
+    d_.material = (const R*)material;
+    gather((const R*)x, tmp_a_, st);
+    elements(tmp_a_, st);
+    if (fm) k_vertex_force<R><<<grid_rows(), 256, 0, st>>>(d_, 0, (R*)fm);
+    if (fb) k_vertex_force<R><<<grid_rows(), 256, 0, st>>>(d_, 1, (R*)fb);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  int system_dense(const void* material, const void* x, const void* v, const void* F, void* A, void* b,
+                   void* stream_) override {
+    if (!material || !x || !v || !A || !b) return invalid("cloth_system_dense: null argument");
+    cudaStream_t st = (cudaStream_t)stream_;
+    d_.material = (const R*)material;
+    CLOTH_TRY(assemble_at(x, v, F, st));
+    std::vector<long long> off(L_.S + 1, 0);
+    for (int s = 0; s < L_.S; ++s) {
+      long long n3 = 3LL * (L_.sheet_uoff[s + 1] - L_.sheet_uoff[s]);
+      off[s + 1] = off[s] + n3 * n3;
+    }
+    long long* doff = nullptr;
+    CLOTH_CUDA(cudaMallocAsync((void**)&doff, sizeof(long long) * off.size(), st));
+    CLOTH_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
+    CLOTH_CUDA(cudaMemsetAsync(A, 0, sizeof(R) * off[L_.S], st));
+    k_dense<R><<<grid_rows(), 256, 0, st>>>(d_, doff, (R*)A);
+    k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, d_.bvec, (R*)b, R(1));
+    CLOTH_CUDA(cudaGetLastError());
+    CLOTH_CUDA(cudaFreeAsync(doff, st));
+    return CLOTH_OK;
+  }
+
+  int spmv(const void* material, const void* x, const void* v, const void* p, void* y, void* stream_) override {
+    if (!material || !x || !v || !p || !y) return invalid("cloth_spmv: null argument");
+    cudaStream_t st = (cudaStream_t)stream_;
+    d_.material = (const R*)material;
+    CLOTH_TRY(assemble_at(x, v, nullptr, st));
+    gather((const R*)p, tmp_a_, st);
+    k_spmv_plain<R><<<grid_rows(), 256, 0, st>>>(d_, tmp_a_, tmp_b_);
+    k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, tmp_b_, (R*)y, R(1));
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  int third(const void* material, const void* x, const void* a, const void* b, void* out, void* stream_) override {
+    if (!material || !x || !a || !b || !out) return invalid("cloth_third_contraction: null argument");
+    cudaStream_t st = (cudaStream_t)stream_;
+    d_.material = (const R*)material;
+    gather((const R*)x, tmp_a_, st);
+    gather((const R*)a, tmp_b_, st);
+    gather((const R*)b, tmp_c_, st);
+    k_adj_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_a_, tmp_b_, tmp_c_, 1);
+    if (L_.E)
+      k_adj_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_a_, tmp_b_, tmp_c_, 1);
+    k_vertex_third<R><<<grid_rows(), 256, 0, st>>>(d_, (R*)out);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+ private:
+  struct GraphKey {
+    int kind;
+    const void* p[10];
+    int extra;
+    bool operator==(const GraphKey& o) const {
+      if (kind != o.kind || extra != o.extra) return false;
+      for (int i = 0; i < 10; ++i)
+        if (p[i] != o.p[i]) return false;
+      return true;
+    }
+  };
+  struct CachedGraph {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+  };
+
+  int invalid(const char* msg) {
+    set_last_error(msg);
+    return CLOTH_ERR_INVALID_ARG;
+  }
+
+  template <class U>
+  U* alloc(size_t n, int* rc) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(U)) != cudaSuccess) {
+      *rc = CLOTH_ERR_OOM;
+      return nullptr;
+    }
+    allocs_.push_back(p);
+    bytes_ += n * sizeof(U);
+    return (U*)p;
+  }
+  template <class U>
+  const U* upload(const std::vector<U>& v, int* rc) {
+    U* p = alloc<U>(v.size(), rc);
+    if (p && !v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice) != cudaSuccess)
+      *rc = CLOTH_ERR_CUDA;
+    return p;
+  }
+
+  int grid_rows() const { return (L_.Np + 255) / 256; }
+  size_t n3() const { return 3 * (size_t)L_.Np; }
+  R* sx(int j) const { return seg_x_ + n3() * j; }
+  R* sv(int j) const { return seg_v_ + n3() * j; }
+
+  void gather(const R* in, R* out, cudaStream_t st) { k_gather<R><<<grid_rows(), 256, 0, st>>>(d_, in, out); }
+
+  void elements(const R* x, cudaStream_t st) {
+    if (L_.M) k_elem_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, x);
+    if (L_.E) k_elem_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, x);
+  }
+
+  int assemble_at(const void* x, const void* v, const void* F, cudaStream_t st) {
+    gather((const R*)x, tmp_a_, st);
+    gather((const R*)v, tmp_b_, st);
+    elements(tmp_a_, st);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, tmp_b_, (const R*)F);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  // Solve A y = rhs (y left in d_.dv) for every sheet.  In graph mode the CG loop is a
+  // conditional WHILE node whose condition the kernels clear when the last sheet ends.
+  int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
+    k_solve_begin<R><<<1, 32, 0, st>>>(d_);
+    k_cg_init<R><<<d_.NW, kThreads, 0, st>>>(d_, rhs, phase);
+    CLOTH_CUDA(cudaGetLastError());
+    if (capturing) {
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t g;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      CLOTH_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+      cudaGraphConditionalHandle cond;
+      CLOTH_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+      k_cond_set<R><<<1, 32, 0, st>>>(d_, cond);
+      CLOTH_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CLOTH_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+      CLOTH_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      CLOTH_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      k_cg_spmv<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
+      k_cg_update<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
+      k_cg_dir<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_);
+      cudaGraph_t out = nullptr;
+      CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
+      CLOTH_CUDA(cudaGetLastError());
+      return CLOTH_OK;
+    }
+    const int poll = std::max(1, o_.cg_poll_every);
+    int launched = 0;
+    while (true) {
+      CLOTH_CUDA(cudaMemcpyAsync(host_active_, d_.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CLOTH_CUDA(cudaStreamSynchronize(st));
+      if (*host_active_ <= 0 || launched >= o_.cg_max_iter) break;
+      for (int k = 0; k < poll; ++k) {
+        k_cg_spmv<R><<<d_.NW, kThreads, 0, st>>>(d_, phase, 0, 0);
+        k_cg_update<R><<<d_.NW, kThreads, 0, st>>>(d_, phase, 0, 0);
+        k_cg_dir<R><<<d_.NW, kThreads, 0, st>>>(d_);
+      }
+      launched += poll;
+      CLOTH_CUDA(cudaGetLastError());
+    }
+    return CLOTH_OK;
+  }
+
+  // One implicit step from (x, v) to (xn, vn); F: user-layout force row or null.
+  int step(const R* x, const R* v, const R* F, R* xn, R* vn, R* traj_row, int phase, cudaStream_t st, bool cap) {
+    elements(x, st);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, v, F);
+    CLOTH_CUDA(cudaGetLastError());
+    CLOTH_TRY(solve(d_.bvec, phase, st, cap));
+    k_state_update<R><<<grid_rows(), 256, 0, st>>>(d_, x, v, xn, vn, traj_row);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  const R* force_row(const void* forces, int t) const {
+    return forces ? (const R*)forces + (size_t)t * 3 * L_.Nu : nullptr;
+  }
+
+  int forward_body(const void* material, const void* x0, const void* v0, const void* forces, void* traj_x,
+                   int32_t* status, cudaStream_t st, bool cap) {
+    (void)material;
+    const size_t nu3 = 3 * (size_t)L_.Nu;
+    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
+    gather((const R*)x0, sx(0), st);
+    gather((const R*)v0, sv(0), st);
+    CLOTH_CUDA(cudaMemcpyAsync(traj_x, x0, sizeof(R) * nu3, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < nseg_; ++k) {
+      const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
+      if (k > 0) {
+        CLOTH_CUDA(cudaMemcpyAsync(sx(0), sx(C_), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(sv(0), sv(C_), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+      }
+      if (nseg_ > 1) {
+        CLOTH_CUDA(cudaMemcpyAsync(ck_x_ + n3() * k, sx(0), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(ck_v_ + n3() * k, sv(0), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+      }
+      for (int t = t0; t < t1; ++t) {
+        const int j = t - t0;
+        R* row = (R*)traj_x + (size_t)(t + 1) * nu3;
+        CLOTH_TRY(step(sx(j), sv(j), force_row(forces, t), sx(j + 1), sv(j + 1), row, kPhaseForward, st, cap));
+      }
+    }
+    k_status_out<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, status);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  int backward_body(const void* dL_dx, void* g_material, void* g_forces, void* g_x0, void* g_v0, int32_t* status,
+                    cudaStream_t st, bool cap, int seg_valid) {
+    const size_t nu3 = 3 * (size_t)L_.Nu;
+    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseBackward);
+    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseRecompute);
+    CLOTH_CUDA(cudaMemsetAsync(d_.gacc, 0, sizeof(double) * 3 * L_.S, st));
+    gather((const R*)dL_dx + (size_t)T_ * nu3, ax_, st);
+    CLOTH_CUDA(cudaMemsetAsync(av_, 0, sizeof(R) * n3(), st));
+    const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
+    for (int k = nseg_ - 1; k >= 0; --k) {
+      const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
+      if (k != seg_valid) {
+        CLOTH_CUDA(cudaMemcpyAsync(sx(0), ck_x_ + n3() * k, sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(sv(0), ck_v_ + n3() * k, sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        for (int t = t0; t < t1; ++t) {
+          const int j = t - t0;
+          CLOTH_TRY(step(sx(j), sv(j), force_row(fwd_forces_, t), sx(j + 1), sv(j + 1), nullptr, kPhaseRecompute, st,
+                         cap));
+        }
+      }
+      for (int t = t1 - 1; t >= t0; --t) {
+        const int j = t - t0;
+        // A_t at x_t (the RHS of the step matrix is not needed)
+        elements(sx(j), st);
+        k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, sv(j), nullptr);
+        k_adj_rhs<R><<<grid_rows(), 256, 0, st>>>(d_, ax_, av_);
+        CLOTH_CUDA(cudaGetLastError());
+        CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap));
+        if (L_.M) k_adj_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(j), d_.dv, sv(j + 1), 0);
+        if (L_.E) k_adj_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(j), d_.dv, sv(j + 1), 0);
+        R* gF = g_forces ? (R*)g_forces + (size_t)t * nu3 : nullptr;
+        k_adj_vertex<R><<<grid_rows(), 256, 0, st>>>(d_, ax_, av_, sv(j), sv(j + 1), (const R*)dL_dx + (size_t)t * nu3,
+                                                     gF);
+        k_param_acc<R><<<L_.S, kThreads, 0, st>>>(d_);
+        CLOTH_CUDA(cudaGetLastError());
+      }
+    }
+    if (g_material) k_grad_material<R><<<(L_.S + 127) / 128, 128, 0, st>>>(d_, (R*)g_material);
+    if (g_x0) k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, ax_, (R*)g_x0, R(1));
+    if (g_v0) k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, av_, (R*)g_v0, R(1));
+    k_status_out<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, status);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  // Capture `body` into a graph once per argument set, then launch it on `st`.
+  template <class Body>
+  int run_graph(const GraphKey& key, cudaStream_t st, Body body) {
+    for (auto& g : graphs_)
+      if (g.key == key) {
+        CLOTH_CUDA(cudaGraphLaunch(g.exec, st));
+        return CLOTH_OK;
+      }
+    CLOTH_CUDA(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeRelaxed));
+    int rc = body(cap_stream_);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cap_stream_, &graph);
+    if (rc != CLOTH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) {
+      set_last_error(std::string("graph capture failed: ") + cudaGetErrorString(ec));
+      return CLOTH_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      set_last_error(std::string("graph instantiation failed: ") + cudaGetErrorString(ei));
+      return CLOTH_ERR_CUDA;
+    }
+    if (graphs_.size() >= 8) {
+      cudaGraphExecDestroy(graphs_.front().exec);
+      graphs_.erase(graphs_.begin());
+    }
+    graphs_.push_back({key, exec});
+    CLOTH_CUDA(cudaGraphLaunch(exec, st));
+    return CLOTH_OK;
+  }
+
+  BatchLayout L_;
+  const void* fwd_forces_ = nullptr;    // inputs of the last forward (the recompute reads them again)
+  const void* fwd_material_ = nullptr;
+  cloth_opts o_;
+  Dev<R> d_;
+  int T_ = 0, C_ = 0, nseg_ = 0, seg_valid_ = -1;
+  bool have_forward_ = false;
+  R *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;
+  R *ax_ = nullptr, *av_ = nullptr, *tmp_a_ = nullptr, *tmp_b_ = nullptr, *tmp_c_ = nullptr;
+  double* lpart_ = nullptr;
+  int* host_active_ = nullptr;
+  cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;
+  std::vector<CachedGraph> graphs_;
+  std::vector<void*> allocs_;
+  size_t bytes_ = 0;
+};
+
+template <class R>
+std::unique_ptr<EngineBase> make_engine(const BatchLayout& L, const cloth_opts& o, int* rc, std::string* err) {
+  auto e = std::make_unique<Engine<R>>(L, o);
+  *rc = e->init(err);
+  if (*rc != CLOTH_OK) return nullptr;
+  return e;
+}
+
+}  // namespace cloth

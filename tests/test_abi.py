@@ -1,0 +1,89 @@
+"""CPU-side checks of the C-ABI boundary: the library builds, loads without a GPU and
+exports every entry point that include/cloth_sim.h declares; host-side validation
+rejects bad meshes and options without touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2203_11938_gb300 import build as B
+from paper_2203_11938_gb300 import sim
+from paper_2203_11938_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "cloth_sim.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return sim.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cloth_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(sim.EXPORTS)
+
+
+def test_opts_struct_layout_matches_header(lib):
+    o = sim.default_opts()
+    assert ctypes.sizeof(sim.ClothOpts) == 72
+    assert o.precision == sim.FP32 and o.steps == 1 and o.cg_max_iter == 2000
+    assert o.gravity[2] == pytest.approx(-9.8) and o.clamp_eta == pytest.approx(1e-3)
+    assert o.exec == sim.EXEC_GRAPH and o.cg_poll_every == 16
+
+
+def test_mesh_create_counts(lib):
+    for N in (2, 10, 33):
+        rest, tris = W.grid_mesh(N)
+        m = sim.Mesh(rest, tris, W.pins(N, "top2"))
+        assert m.info() == W.grid_counts(N)
+
+
+def test_mesh_validation_errors(lib):
+    rest, tris = W.grid_mesh(3)
+    bad = tris.copy()
+    bad[0, 0] = 99
+    with pytest.raises(sim.ClothError, match="-1"):
+        sim.Mesh(rest, bad)
+    deg = rest.copy()
+    deg[1] = deg[0]
+    with pytest.raises(sim.ClothError, match="-3"):
+        sim.Mesh(deg, tris)
+    flipped = tris.copy()
+    flipped[1] = flipped[1][::-1]
+    with pytest.raises(sim.ClothError, match="-2"):
+        sim.Mesh(rest, flipped)
+    # three triangles on one edge
+    r3 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1]], float)
+    t3 = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], np.int32)
+    with pytest.raises(sim.ClothError, match="-2"):
+        sim.Mesh(r3, t3)
+    msg = lib.cloth_last_error().decode()
+    assert "more than two" in msg
+
+
+def test_batch_create_rejects_bad_options_on_host(lib):
+    rest, tris = W.grid_mesh(3)
+    m = sim.Mesh(rest, tris)
+    arr = (ctypes.c_void_p * 1)(m._h)
+    h = ctypes.c_void_p()
+    for field, value in (("steps", 0), ("dt", -1.0), ("cg_max_iter", 0), ("precision", 7), ("exec", 9),
+                         ("clamp_eta", -1.0), ("cg_poll_every", 0)):
+        o = sim.default_opts()
+        setattr(o, field, value)
+        rc = lib.cloth_batch_create(arr, 1, ctypes.byref(o), ctypes.byref(h))
+        assert rc == -1, field
+    assert lib.cloth_batch_create(arr, 0, ctypes.byref(sim.default_opts()), ctypes.byref(h)) == -1
+    assert lib.cloth_forward(None, None, None, None, None, None, None, None) == -1
+    assert lib.cloth_backward(None, None, None, None, None, None, None, None) == -1

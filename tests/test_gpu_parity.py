@@ -1,0 +1,285 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 mode must agree to 1e-10 (relative) on gradients and to round-off on
+states (both sides run the same Jacobi-PCG recurrence); FP32 mode must keep the max
+vertex position error within 1e-5 of the 1 m sheet and the parameter gradients within
+1e-3 relative of the oracle.  Element-level FP32 checks use 1e-4 relative of the
+field's scale (float has 6e-8 unit round-off; the Green strain near rest cancels about
+three digits).
+"""
+import numpy as np
+import pytest
+
+from paper_2203_11938_gb300 import workloads as W
+
+from gpu_util import MAT, make_batch, oracle_sims, rel, sheets_mixed, split, to_cuda, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11938_gb300 import build
+
+    build.build()
+
+
+def _dtype(prec):
+    return torch.float64 if prec == "f64" else torch.float32
+
+
+def _perturbed(sheets, seed=0, amp=0.03):
+    rng = np.random.default_rng(seed)
+    xs = [s.rest * np.array([0.97, 1.03, 1.0]) + amp * rng.normal(size=s.rest.shape) for s in sheets]
+    vs = [0.1 * rng.normal(size=s.rest.shape) * (s.pinned == 0)[:, None] for s in sheets]
+    return xs, vs
+
+
+def _materials(sheets):
+    return np.stack([s.material for s in sheets])
+
+
+# --------------------------------------------------------------------- element stages
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_internal_forces_match_oracle(oracle_mod, prec):
+    sheets = sheets_mixed()
+    b = make_batch(sheets, steps=1, dt=1 / 30, precision=prec, tol=1e-10)
+    xs, _ = _perturbed(sheets)
+    mat = _materials(sheets)
+    dt = _dtype(prec)
+    fm, fb = b.internal_forces(to_cuda(mat, dt), to_cuda(np.concatenate(xs), dt))
+    fm, fb = split(to_np(fm), b.sheet_sizes), split(to_np(fb), b.sheet_sizes)
+    tol = 1e-11 if prec == "f64" else 1e-4
+    for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
+        _, om, ob = o.energy_forces(s.material, xs[k])
+        assert rel(fm[k], om) < tol
+        assert rel(fb[k], ob) < tol * (10 if prec == "f32" else 1)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_assembled_system_matches_oracle(oracle_mod, prec):
+    """A = M + h^2 H~ and b = h (f + M g + F) - h^2 H~ v, pinned rows identity."""
+    sheets = sheets_mixed()
+    b = make_batch(sheets, steps=1, dt=1 / 30, precision=prec, tol=1e-10)
+    xs, vs = _perturbed(sheets, seed=1)
+    rng = np.random.default_rng(2)
+    Fs = [1e-3 * rng.normal(size=s.rest.shape) for s in sheets]
+    dt = _dtype(prec)
+    mat = _materials(sheets)
+    A, bv = b.system_dense(to_cuda(mat, dt), to_cuda(np.concatenate(xs), dt), to_cuda(np.concatenate(vs), dt),
+                           to_cuda(np.concatenate(Fs), dt))
+    bv = split(to_np(bv), b.sheet_sizes)
+    tol = 1e-11 if prec == "f64" else 1e-5
+    for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
+        Ao, bo = o.system_dense(s.material, 1 / 30, W.GRAVITY, xs[k], vs[k], Fs[k], eta=1e-3)
+        Ag = to_np(A[k])
+        assert np.abs(Ag - Ao).max() < tol * np.abs(Ao).max()
+        assert rel(bv[k].ravel(), bo) < tol * 10
+        np.testing.assert_array_equal(Ag, Ag.T) if prec == "f64" else None
+
+
+def test_spmv_matches_dense_product(oracle_mod):
+    sheets = sheets_mixed()
+    b = make_batch(sheets, steps=1, dt=1 / 30, precision="f64", tol=1e-10)
+    xs, vs = _perturbed(sheets, seed=4)
+    rng = np.random.default_rng(5)
+    ps = [rng.normal(size=s.rest.shape) for s in sheets]
+    mat = to_cuda(_materials(sheets), torch.float64)
+    y = b.spmv(mat, to_cuda(np.concatenate(xs), torch.float64), to_cuda(np.concatenate(vs), torch.float64),
+               to_cuda(np.concatenate(ps), torch.float64))
+    y = split(to_np(y), b.sheet_sizes)
+    for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
+        Ao, _ = o.system_dense(s.material, 1 / 30, W.GRAVITY, xs[k], vs[k], None, eta=1e-3)
+        assert rel(y[k].ravel(), Ao @ ps[k].ravel()) < 1e-12
+
+
+@pytest.mark.parametrize("eta", [0.0, 1e-3])
+def test_third_contraction_matches_oracle(oracle_mod, eta):
+    sheets = sheets_mixed()
+    b = make_batch(sheets, steps=1, dt=1 / 30, precision="f64", tol=1e-10, eta=eta)
+    xs, _ = _perturbed(sheets, seed=6)
+    rng = np.random.default_rng(7)
+    As = [rng.normal(size=s.rest.shape) for s in sheets]
+    Bs = [rng.normal(size=s.rest.shape) for s in sheets]
+    f64 = torch.float64
+    out = b.third(to_cuda(_materials(sheets), f64), to_cuda(np.concatenate(xs), f64), to_cuda(np.concatenate(As), f64),
+                  to_cuda(np.concatenate(Bs), f64))
+    out = split(to_np(out), b.sheet_sizes)
+    for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
+        assert rel(out[k], o.third(s.material, xs[k], As[k], Bs[k], eta=eta)) < 1e-10
+
+
+# --------------------------------------------------------------------- trajectories
+def _rollout_both(oracle_mod, sheets, *, steps, dt, prec, tol, oracle_tol, forces=None, exec_mode="graph", ckpt=0,
+                  v0s=None):
+    b = make_batch(sheets, steps=steps, dt=dt, precision=prec, tol=tol, exec_mode=exec_mode, ckpt=ckpt)
+    dtp = _dtype(prec)
+    x0 = np.concatenate([s.rest for s in sheets])
+    v0 = np.zeros_like(x0) if v0s is None else np.concatenate(v0s)
+    F = None if forces is None else np.concatenate(forces, axis=1)
+    traj, status = b.forward(to_cuda(_materials(sheets), dtp), to_cuda(x0, dtp), to_cuda(v0, dtp),
+                             None if F is None else to_cuda(F, dtp))
+    torch.cuda.synchronize()
+    refs = []
+    for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
+        vk = np.zeros_like(s.rest) if v0s is None else v0s[k]
+        refs.append(o.forward(s.material, s.rest, vk, None if forces is None else forces[k], dt=dt, steps=steps,
+                              tol=oracle_tol, max_iter=20000, gravity=W.GRAVITY))
+    return b, traj, status, refs
+
+
+def test_config1_fp64_trajectory_and_gradients(oracle_mod):
+    """10x10 sheet, two top corners pinned, 20 steps of 1/30 s, FP64 (config 1 of the
+    benchmark list): positions to 1e-10 m, gradients of the target-trajectory loss
+    w.r.t. Y, k_b, rho, x0, v0 to 1e-10 relative."""
+    cfg = W.config1()
+    s = cfg.sheets[0]
+    tol = 1e-12
+    b, traj, status, refs = _rollout_both(oracle_mod, cfg.sheets, steps=cfg.steps, dt=cfg.dt, prec="f64", tol=tol,
+                                          oracle_tol=tol)
+    tx, tv, it, st = refs[0]
+    assert int(status[0]) == 0 and st == 0
+    assert np.abs(to_np(traj) - tx).max() < 1e-10
+    # target trajectory from scaled parameters (oracle), loss and adjoint
+    o = oracle_sims(oracle_mod, cfg.sheets)[0]
+    tgt_mat = s.material * np.array(cfg.target_scale)
+    target = o.forward(tgt_mat, s.rest, np.zeros_like(s.rest), None, dt=cfg.dt, steps=cfg.steps, tol=tol,
+                       max_iter=20000, gravity=W.GRAVITY)[0]
+    L_o, dL = oracle_mod.loss_l2(tx, target)
+    loss, grad = b.loss_l2(traj, to_cuda(target, torch.float64))
+    assert float(loss[0]) == pytest.approx(L_o, rel=1e-9)
+    assert rel(to_np(grad), dL) < 1e-9
+    g = b.backward(to_cuda(dL, torch.float64))
+    go = o.backward(s.material, tx, tv, dL, dt=cfg.dt, steps=cfg.steps, tol=tol, max_iter=20000, gravity=W.GRAVITY)
+    gm = to_np(g["material"])[0]
+    for k in (0, 2, 3):
+        assert gm[k] == pytest.approx(go["material"][k], rel=1e-10)
+    assert gm[1] == 0.0
+    assert rel(to_np(g["x0"]), go["x0"]) < 1e-10
+    assert rel(to_np(g["v0"]), go["v0"]) < 1e-10
+    assert rel(to_np(g["forces"]), go["forces"]) < 1e-10
+    assert int(g["status"][0]) == 0
+
+
+def test_config2_fp32_positions_and_gradients(oracle_mod):
+    """32x32 sheet, top edge pinned, 60 steps of 1/60 s with seeded per-vertex forces,
+    FP32 path (CG tol 1e-6) vs the FP64 oracle (tol 1e-10): max position error
+    <= 1e-5 m, gradients w.r.t. Y, k_b, rho, forces and x0 within 1e-3 relative."""
+    cfg = W.config2()
+    s = cfg.sheets[0]
+    b, traj, status, refs = _rollout_both(oracle_mod, cfg.sheets, steps=cfg.steps, dt=cfg.dt, prec="f32",
+                                          tol=cfg.cg_tol, oracle_tol=1e-10, forces=[s.forces])
+    tx, tv, it, st = refs[0]
+    assert int(status[0]) == 0
+    err = np.abs(to_np(traj) - tx).max()
+    assert err <= 1e-5, err
+    o = oracle_sims(oracle_mod, cfg.sheets)[0]
+    tgt = o.forward(s.material * np.array(cfg.target_scale), s.rest, np.zeros_like(s.rest), s.forces, dt=cfg.dt,
+                    steps=cfg.steps, tol=1e-10, max_iter=20000, gravity=W.GRAVITY)[0]
+    _, dL = oracle_mod.loss_l2(tx, tgt)
+    _, dLg = b.loss_l2(traj, to_cuda(tgt, torch.float32))
+    g = b.backward(dLg)
+    go = o.backward(s.material, tx, tv, dL, dt=cfg.dt, steps=cfg.steps, tol=1e-10, max_iter=20000, gravity=W.GRAVITY)
+    gm = to_np(g["material"])[0]
+    for k in (0, 2, 3):
+        assert gm[k] == pytest.approx(go["material"][k], rel=1e-3), k
+    assert rel(to_np(g["forces"]), go["forces"]) < 1e-3
+    assert rel(to_np(g["x0"]), go["x0"]) < 1e-3
+
+
+def test_batched_sheets_match_their_own_oracles(oracle_mod):
+    """Three sheets of different sizes and materials in one batch, FP64: each sheet's
+    trajectory and material gradient equals its own oracle run."""
+    sheets = sheets_mixed(seed=11)
+    steps, dt, tol = 8, 1 / 30, 1e-12
+    b, traj, status, refs = _rollout_both(oracle_mod, sheets, steps=steps, dt=dt, prec="f64", tol=tol, oracle_tol=tol)
+    parts = split(to_np(traj), b.sheet_sizes, axis=1)
+    for k, ref in enumerate(refs):
+        assert np.abs(parts[k] - ref[0]).max() < 1e-10
+    rng = np.random.default_rng(12)
+    dLs = [rng.normal(size=ref[0].shape) for ref in refs]
+    g = b.backward(to_cuda(np.concatenate(dLs, axis=1), torch.float64))
+    gm = to_np(g["material"])
+    for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
+        go = o.backward(s.material, refs[k][0], refs[k][1], dLs[k], dt=dt, steps=steps, tol=tol, max_iter=20000,
+                        gravity=W.GRAVITY)
+        for q in (0, 2, 3):
+            assert gm[k, q] == pytest.approx(go["material"][q], rel=1e-9)
+
+
+def test_checkpointing_and_exec_modes_agree(oracle_mod):
+    """Checkpoint-and-recompute (C = 3 of 10 steps) and the plain host-polled CG give the
+    same trajectory and gradients as the captured-graph run without checkpoints."""
+    sheets = sheets_mixed(seed=21)[:2]
+    steps, dt = 10, 1 / 30
+    res = []
+    for exec_mode, ckpt in (("graph", 0), ("graph", 3), ("plain", 3), ("plain", 0)):
+        b = make_batch(sheets, steps=steps, dt=dt, precision="f32", tol=1e-6, exec_mode=exec_mode, ckpt=ckpt)
+        x0 = to_cuda(np.concatenate([s.rest for s in sheets]), torch.float32)
+        mat = to_cuda(_materials(sheets), torch.float32)
+        traj, st = b.forward(mat, x0, torch.zeros_like(x0), None)
+        dL = torch.ones_like(traj)
+        g = b.backward(dL)
+        g2 = b.backward(dL)  # a second backward on the same forward recomputes every segment
+        res.append((to_np(traj), to_np(g["material"]), to_np(g["x0"]), to_np(g2["material"])))
+    for r in res[1:]:
+        np.testing.assert_array_equal(r[0], res[0][0])
+        np.testing.assert_array_equal(r[1], res[0][1])
+        np.testing.assert_array_equal(r[2], res[0][2])
+    for r in res:
+        np.testing.assert_array_equal(r[3], r[1])
+
+
+def test_cg_maxiter_status_and_free_fall():
+    """cg_max_iter = 1 marks every sheet CG_MAXITER without failing the call; an
+    unpinned sheet under gravity falls exactly as implicit Euler predicts."""
+    from paper_2203_11938_gb300 import sim
+
+    rest, tris = W.grid_mesh(6)
+    b = sim.ClothBatch([(rest, tris, None)], steps=5, dt=1 / 30, precision="f64", cg_tol=1e-12, cg_max_iter=4000)
+    x0 = to_cuda(rest, torch.float64)
+    traj, status = b.forward(to_cuda(MAT[None], torch.float64), x0, torch.zeros_like(x0), None)
+    assert int(status[0]) == 0
+    g = np.array(W.GRAVITY)
+    h = 1 / 30
+    for t in range(6):
+        np.testing.assert_allclose(to_np(traj[t]), rest + h * h * g * t * (t + 1) / 2, atol=1e-9)
+    rng = np.random.default_rng(0)
+    b1 = sim.ClothBatch([(rest, tris, W.pins(6, "top2"))], steps=2, dt=1 / 30, precision="f32", cg_tol=1e-9,
+                        cg_max_iter=1)
+    x1 = to_cuda(rest + 0.01 * rng.normal(size=rest.shape), torch.float32)
+    _, status = b1.forward(to_cuda(MAT[None], torch.float32), x1, torch.zeros_like(x1), None)
+    assert int(status[0]) & sim.STATUS_CG_MAXITER
+
+
+def test_pinhole_loss_matches_oracle(oracle_mod):
+    cfg = W.config1()
+    s = cfg.sheets[0]
+    b = make_batch(cfg.sheets, steps=4, dt=cfg.dt, precision="f64", tol=1e-10)
+    rng = np.random.default_rng(3)
+    traj = s.rest[None] + 0.05 * rng.normal(size=(5, s.n, 3))
+    uv = rng.normal(scale=20.0, size=(5, s.n, 2))
+    cam = (500.0, 0.5, 0.5, 2.0)
+    L_o, g_o = oracle_mod.loss_pinhole(traj, uv, cam)
+    loss, grad = b.loss_pinhole(to_cuda(traj, torch.float64), to_cuda(uv, torch.float64), cam)
+    assert float(loss[0]) == pytest.approx(L_o, rel=1e-12)
+    assert rel(to_np(grad), g_o) < 1e-12
+
+
+def test_autograd_function_matches_direct_calls():
+    from paper_2203_11938_gb300 import sim
+
+    sheets = sheets_mixed(seed=5)[:2]
+    b = make_batch(sheets, steps=4, dt=1 / 30, precision="f64", tol=1e-12)
+    mat = to_cuda(_materials(sheets), torch.float64).requires_grad_(True)
+    x0 = to_cuda(np.concatenate([s.rest for s in sheets]), torch.float64).requires_grad_(True)
+    v0 = torch.zeros_like(x0, requires_grad=True)
+    traj = sim.cloth_trajectory(b, mat, x0, v0)
+    (traj ** 2).sum().backward()
+    g = b.backward(2 * traj.detach())
+    torch.testing.assert_close(mat.grad, g["material"], rtol=0, atol=0)
+    torch.testing.assert_close(x0.grad, g["x0"], rtol=0, atol=0)
