@@ -117,7 +117,11 @@ int cloth_batch_info(const cloth_batch* batch, int32_t* total_vertices, int32_t*
  * x0, v0: device [N_total][3]; forces: device [steps][N_total][3] newtons, or NULL
  * for none; traj_x: device [steps + 1][N_total][3], written (traj_x[0] = x0);
  * status: device [count] int32, written with CLOTH_STATUS_* bits.
- * Keeps internally what cloth_backward needs (checkpoints). */
+ * Keeps internally what cloth_backward needs: a copy of `material` and the
+ * checkpointed states.  `forces` is read again by the backward's recompute, so its
+ * contents must stay unchanged until the matching cloth_backward has been issued.
+ * The state (x, v) is carried in double internally in both precisions; element
+ * edge vectors are formed from it before rounding to the batch precision. */
 int cloth_forward(cloth_batch* batch, const void* material, const void* x0, const void* v0,
                   const void* forces, void* traj_x, int32_t* status, void* stream);
 

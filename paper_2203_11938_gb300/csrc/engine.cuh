@@ -157,22 +157,47 @@ __device__ __forceinline__ void finish_sheet(const Dev<R>& d, int s, int phase, 
 }
 
 // ------------------------------------------------------------------ layout moves
-template <class R>
-__global__ void k_gather(Dev<R> d, const R* __restrict__ in, R* __restrict__ out) {
+template <class R, class Tin, class Tout>
+__global__ void k_gather(Dev<R> d, const Tin* __restrict__ in, Tout* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   const int u = d.i2u[i];
-  st3(out, i, u >= 0 && in ? ld3(in, u) : V3<R>{R(0), R(0), R(0)});
+  V3<Tout> v = {Tout(0), Tout(0), Tout(0)};
+  if (u >= 0 && in) {
+    const V3<Tin> w = ld3(in, u);
+    v = {(Tout)w.x, (Tout)w.y, (Tout)w.z};
+  }
+  st3(out, i, v);
 }
 
-template <class R>
-__global__ void k_scatter(Dev<R> d, const R* __restrict__ in, R* __restrict__ out, R s) {
+template <class R, class Tin>
+__global__ void k_scatter(Dev<R> d, const Tin* __restrict__ in, R* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   const int u = d.i2u[i];
   if (u < 0) return;
-  V3<R> v = ld3(in, i);
-  st3(out, u, V3<R>{s * v.x, s * v.y, s * v.z});
+  const V3<Tin> v = ld3(in, i);
+  st3(out, u, V3<R>{(R)v.x, (R)v.y, (R)v.z});
+}
+
+// Element positions relative to the element's first vertex: the differences are
+// formed from the FP64 state before rounding to R, so FP32 element arithmetic sees
+// edge vectors with full relative precision.
+template <class R, int K>
+__device__ __forceinline__ void load_relative(const double* __restrict__ x, const int* idx, V3<R>* out) {
+  const V3<double> x0 = ld3(x, idx[0]);
+  out[0] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int a = 1; a < K; ++a) {
+    const V3<double> xa = ld3(x, idx[a]);
+    out[a] = {(R)(xa.x - x0.x), (R)(xa.y - x0.y), (R)(xa.z - x0.z)};
+  }
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> ld3r(const double* __restrict__ x, int i) {
+  const V3<double> v = ld3(x, i);
+  return {(R)v.x, (R)v.y, (R)v.z};
 }
 
 // ------------------------------------------------------------------ element kernels
@@ -203,14 +228,16 @@ __device__ __forceinline__ HingeConst<R> hinge_const(const Dev<R>& d, int e) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const R* __restrict__ x) {
+__global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const double* __restrict__ x) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.M) return;
   TriConst<R> k = tri_const(d, t);
   V3<R> xe[3], f[3];
   R H[6][9];
+  int idx[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) xe[a] = ld3(x, d.tri_v[(size_t)a * d.M + t]);
+  for (int a = 0; a < 3; ++a) idx[a] = d.tri_v[(size_t)a * d.M + t];
+  load_relative<R, 3>(x, idx, xe);
   membrane_force_hessian(k, xe, d.clamp, f, H);
   R* fo = d.tri_f + 9 * (size_t)t;
 #pragma unroll
@@ -227,14 +254,16 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const R* __
 }
 
 template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const R* __restrict__ x) {
+__global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const double* __restrict__ x) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   HingeConst<R> k = hinge_const(d, e);
   V3<R> xe[4], f[4];
   R H[10][9];
+  int idx[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) xe[a] = ld3(x, d.hin_v[(size_t)a * d.E + e]);
+  for (int a = 0; a < 4; ++a) idx[a] = d.hin_v[(size_t)a * d.E + e];
+  load_relative<R, 4>(x, idx, xe);
   bending_force_hessian(k, xe, f, H);
   R* fo = d.hin_f + 12 * (size_t)e;
 #pragma unroll
@@ -281,7 +310,7 @@ __device__ __forceinline__ void gather_block(const Dev<R>& d, int ent, R (&Hb)[9
 // Assembly of A, b, D^{-1} (one thread per row; a warp is one SELL slice).
 // Fext: user-layout external force of this step or null.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __restrict__ v, const R* __restrict__ Fext) {
+__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const double* __restrict__ v, const R* __restrict__ Fext) {
   const int w = blockIdx.x;
   const int s = d.work_sheet[w];
   if (threadIdx.x >= d.work_rows[w]) return;
@@ -306,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
     const int j = d.cols[ent];
     R Hb[9];
     gather_block(d, ent, Hb);
-    const V3<R> vj = ld3(v, j);
+    const V3<R> vj = ld3r<R>(v, j);
     Hv.x += Hb[0] * vj.x + Hb[1] * vj.y + Hb[2] * vj.z;
     Hv.y += Hb[3] * vj.x + Hb[4] * vj.y + Hb[5] * vj.z;
     Hv.z += Hb[6] * vj.x + Hb[7] * vj.y + Hb[8] * vj.z;
@@ -477,17 +506,19 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
 
 // v' = v + dv, x' = x + h v'; optional user-layout copy of x'.
 template <class R>
-__global__ void k_state_update(Dev<R> d, const R* __restrict__ x, const R* __restrict__ v, R* __restrict__ xn,
-                               R* __restrict__ vn, R* __restrict__ traj_row) {
+__global__ void k_state_update(Dev<R> d, const double* __restrict__ x, const double* __restrict__ v,
+                               double* __restrict__ xn, double* __restrict__ vn, R* __restrict__ traj_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   const V3<R> dv = ld3(d.dv, i);
-  const V3<R> v1 = add3(ld3(v, i), dv);
-  const V3<R> x1 = axpy3(d.h, v1, ld3(x, i));
+  const V3<double> v0 = ld3(v, i), x0 = ld3(x, i);
+  const V3<double> v1 = {v0.x + (double)dv.x, v0.y + (double)dv.y, v0.z + (double)dv.z};
+  const double h = (double)d.h;
+  const V3<double> x1 = {x0.x + h * v1.x, x0.y + h * v1.y, x0.z + h * v1.z};
   st3(vn, i, v1);
   st3(xn, i, x1);
   const int u = d.i2u[i];
-  if (traj_row && u >= 0) st3(traj_row, u, x1);
+  if (traj_row && u >= 0) st3(traj_row, u, V3<R>{(R)x1.x, (R)x1.y, (R)x1.z});
 }
 
 template <class R>
@@ -506,19 +537,21 @@ __global__ void k_status_out(Dev<R> d, int32_t* status) {
 // ------------------------------------------------------------------ adjoint kernels
 // mode 0: adjoint step contributions; mode 1: third-derivative contraction only.
 template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const R* __restrict__ x,
-                                                         const R* __restrict__ lam, const R* __restrict__ u, int mode) {
+__global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const double* __restrict__ x,
+                                                         const R* __restrict__ lam, const double* __restrict__ u,
+                                                         int mode) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.M) return;
   TriConst<R> k = tri_const(d, t);
   V3<R> xe[3], le[3], ue[3], f[3], Hx[3], Hl[3], Hu[3], th[3];
+  int idx[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int vi = d.tri_v[(size_t)a * d.M + t];
-    xe[a] = ld3(x, vi);
-    le[a] = ld3(lam, vi);
-    ue[a] = ld3(u, vi);
+    idx[a] = d.tri_v[(size_t)a * d.M + t];
+    le[a] = ld3(lam, idx[a]);
+    ue[a] = ld3r<R>(u, idx[a]);
   }
+  load_relative<R, 3>(x, idx, xe);
   membrane_adjoint(k, xe, le, ue, d.clamp, f, Hx, Hl, Hu, th);
   const R h = d.h, h2 = d.h * d.h;
   R* ro = d.tri_r + 18 * (size_t)t;
@@ -548,19 +581,21 @@ __global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const R* __r
 }
 
 template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_adj_hinge(Dev<R> d, const R* __restrict__ x,
-                                                           const R* __restrict__ lam, const R* __restrict__ u, int mode) {
+__global__ void __launch_bounds__(kElemThreads) k_adj_hinge(Dev<R> d, const double* __restrict__ x,
+                                                           const R* __restrict__ lam, const double* __restrict__ u,
+                                                           int mode) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   HingeConst<R> k = hinge_const(d, e);
   V3<R> xe[4], le[4], ue[4], f[4], Hl[4], Hu[4], th[4];
+  int idx[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const int vi = d.hin_v[(size_t)a * d.E + e];
-    xe[a] = ld3(x, vi);
-    le[a] = ld3(lam, vi);
-    ue[a] = ld3(u, vi);
+    idx[a] = d.hin_v[(size_t)a * d.E + e];
+    le[a] = ld3(lam, idx[a]);
+    ue[a] = ld3r<R>(u, idx[a]);
   }
+  load_relative<R, 4>(x, idx, xe);
   bending_adjoint(k, xe, le, ue, f, Hl, Hu, th);
   const R h = d.h, h2 = d.h * d.h;
   R* ro = d.hin_r + 24 * (size_t)e;
@@ -606,8 +641,8 @@ __global__ void k_adj_rhs(Dev<R> d, const R* __restrict__ ax, const R* __restric
 
 // Per-vertex adjoint update after the element pass; lam = d.dv.
 template <class R>
-__global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, const R* __restrict__ v_t,
-                             const R* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row) {
+__global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, const double* __restrict__ v_t,
+                             const double* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   V3<R> r1 = {R(0), R(0), R(0)}, r2 = {R(0), R(0), R(0)};
@@ -626,13 +661,11 @@ __global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, c
   st3(ax, i, V3<R>{a_x.x + r1.x + dl.x, a_x.y + r1.y + dl.y, a_x.z + r1.z + dl.z});
   st3(av, i, V3<R>{a_v.x + d.h * a_x.x + r2.x, a_v.y + d.h * a_x.y + r2.y, a_v.z + d.h * a_x.z + r2.z});
   if (gF_row && u >= 0) st3(gF_row, u, V3<R>{d.h * lam.x, d.h * lam.y, d.h * lam.z});
-  const V3<R> vt = ld3(v_t, i), vt1 = ld3(v_t1, i);
-  const int s = d.vsheet[i];
+  const V3<double> vt = ld3(v_t, i), vt1 = ld3(v_t1, i);
   const double m1 = (double)d.area3[i];
-  d.row_sc[i] = m1 * ((double)lam.x * ((double)d.h * (double)d.gx - ((double)vt1.x - (double)vt.x)) +
-                      (double)lam.y * ((double)d.h * (double)d.gy - ((double)vt1.y - (double)vt.y)) +
-                      (double)lam.z * ((double)d.h * (double)d.gz - ((double)vt1.z - (double)vt.z)));
-  (void)s;
+  d.row_sc[i] = m1 * ((double)lam.x * ((double)d.h * (double)d.gx - (vt1.x - vt.x)) +
+                      (double)lam.y * ((double)d.h * (double)d.gy - (vt1.y - vt.y)) +
+                      (double)lam.z * ((double)d.h * (double)d.gz - (vt1.z - vt.z)));
 }
 
 // Per-sheet accumulation of the material gradients (deterministic).

@@ -117,17 +117,23 @@ class Engine final : public EngineBase {
     d.active = alloc<int>(1, &rc);
     d.iter_total = alloc<unsigned long long>(3, &rc);
     d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
-    seg_x_ = alloc<R>(n3 * (C_ + 1), &rc);
-    seg_v_ = alloc<R>(n3 * (C_ + 1), &rc);
+    // the state (x, v) is carried in FP64 in both precisions
+    seg_x_ = alloc<double>(n3 * (C_ + 1), &rc);
+    seg_v_ = alloc<double>(n3 * (C_ + 1), &rc);
     if (nseg_ > 1) {
-      ck_x_ = alloc<R>(n3 * nseg_, &rc);
-      ck_v_ = alloc<R>(n3 * nseg_, &rc);
+      ck_x_ = alloc<double>(n3 * nseg_, &rc);
+      ck_v_ = alloc<double>(n3 * nseg_, &rc);
     }
     ax_ = alloc<R>(n3, &rc);
     av_ = alloc<R>(n3, &rc);
     tmp_a_ = alloc<R>(n3, &rc);
     tmp_b_ = alloc<R>(n3, &rc);
-    tmp_c_ = alloc<R>(n3, &rc);
+    tmp_xd_ = alloc<double>(n3, &rc);
+    tmp_vd_ = alloc<double>(n3, &rc);
+    tmp_ud_ = alloc<double>(n3, &rc);
+    mat_ = alloc<R>(4 * (size_t)L_.S, &rc);
+    mat_tmp_ = alloc<R>(4 * (size_t)L_.S, &rc);
+    d.material = mat_;
     lpart_ = alloc<double>((size_t)L_.S * T_, &rc);
     if (rc != CLOTH_OK) {
       *err = "device allocation failed";
@@ -158,8 +164,7 @@ class Engine final : public EngineBase {
     }
     cudaStream_t st = (cudaStream_t)stream_;
     last_stream_ = st;
-    d_.material = (const R*)material;
-    fwd_material_ = material;
+    d_.material = mat_;
     fwd_forces_ = forces;
     if (o_.exec == CLOTH_EXEC_GRAPH) {
       GraphKey key{0, {material, x0, v0, forces, traj_x, status, nullptr, nullptr, nullptr, nullptr}, 0};
@@ -186,10 +191,10 @@ class Engine final : public EngineBase {
     }
     cudaStream_t st = (cudaStream_t)stream_;
     last_stream_ = st;
-    d_.material = (const R*)fwd_material_;
+    d_.material = mat_;
     const int seg_valid = seg_valid_;
     if (o_.exec == CLOTH_EXEC_GRAPH) {
-      GraphKey key{1, {fwd_material_, fwd_forces_, dL_dx, g_material, g_forces, g_x0, g_v0, status, nullptr, nullptr},
+      GraphKey key{1, {fwd_forces_, dL_dx, g_material, g_forces, g_x0, g_v0, status, nullptr, nullptr, nullptr},
                    seg_valid};
       CLOTH_TRY(run_graph(key, st, [&](cudaStream_t s) {
         return backward_body(dL_dx, g_material, g_forces, g_x0, g_v0, status, s, true, seg_valid);
@@ -246,11 +251,12 @@ class Engine final : public EngineBase {
   int internal_forces(const void* material, const void* x, void* fm, void* fb, void* stream_) override {
     if (!material || !x) return invalid("cloth_internal_forces: material and x must be non-null");
     cudaStream_t st = (cudaStream_t)stream_;
-    d_.material = (const R*)material;
-    gather((const R*)x, tmp_a_, st);
-    elements(tmp_a_, st);
+    CLOTH_TRY(use_material(material, st));
+    gather_state((const R*)x, tmp_xd_, st);
+    elements(tmp_xd_, st);
     if (fm) k_vertex_force<R><<<grid_rows(), 256, 0, st>>>(d_, 0, (R*)fm);
     if (fb) k_vertex_force<R><<<grid_rows(), 256, 0, st>>>(d_, 1, (R*)fb);
+    d_.material = mat_;
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -259,7 +265,7 @@ class Engine final : public EngineBase {
                    void* stream_) override {
     if (!material || !x || !v || !A || !b) return invalid("cloth_system_dense: null argument");
     cudaStream_t st = (cudaStream_t)stream_;
-    d_.material = (const R*)material;
+    CLOTH_TRY(use_material(material, st));
     CLOTH_TRY(assemble_at(x, v, F, st));
     std::vector<long long> off(L_.S + 1, 0);
     for (int s = 0; s < L_.S; ++s) {
@@ -271,7 +277,8 @@ class Engine final : public EngineBase {
     CLOTH_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
     CLOTH_CUDA(cudaMemsetAsync(A, 0, sizeof(R) * off[L_.S], st));
     k_dense<R><<<grid_rows(), 256, 0, st>>>(d_, doff, (R*)A);
-    k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, d_.bvec, (R*)b, R(1));
+    k_scatter<R, R><<<grid_rows(), 256, 0, st>>>(d_, d_.bvec, (R*)b);
+    d_.material = mat_;
     CLOTH_CUDA(cudaGetLastError());
     CLOTH_CUDA(cudaFreeAsync(doff, st));
     return CLOTH_OK;
@@ -280,11 +287,12 @@ class Engine final : public EngineBase {
   int spmv(const void* material, const void* x, const void* v, const void* p, void* y, void* stream_) override {
     if (!material || !x || !v || !p || !y) return invalid("cloth_spmv: null argument");
     cudaStream_t st = (cudaStream_t)stream_;
-    d_.material = (const R*)material;
+    CLOTH_TRY(use_material(material, st));
     CLOTH_TRY(assemble_at(x, v, nullptr, st));
     gather((const R*)p, tmp_a_, st);
     k_spmv_plain<R><<<grid_rows(), 256, 0, st>>>(d_, tmp_a_, tmp_b_);
-    k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, tmp_b_, (R*)y, R(1));
+    k_scatter<R, R><<<grid_rows(), 256, 0, st>>>(d_, tmp_b_, (R*)y);
+    d_.material = mat_;
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -292,14 +300,16 @@ class Engine final : public EngineBase {
   int third(const void* material, const void* x, const void* a, const void* b, void* out, void* stream_) override {
     if (!material || !x || !a || !b || !out) return invalid("cloth_third_contraction: null argument");
     cudaStream_t st = (cudaStream_t)stream_;
-    d_.material = (const R*)material;
-    gather((const R*)x, tmp_a_, st);
-    gather((const R*)a, tmp_b_, st);
-    gather((const R*)b, tmp_c_, st);
-    k_adj_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_a_, tmp_b_, tmp_c_, 1);
+    CLOTH_TRY(use_material(material, st));
+    gather_state((const R*)x, tmp_xd_, st);
+    gather((const R*)a, tmp_a_, st);
+    gather_state((const R*)b, tmp_ud_, st);
+    k_adj_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_xd_, tmp_a_, tmp_ud_, 1);
     if (L_.E)
-      k_adj_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_a_, tmp_b_, tmp_c_, 1);
+      k_adj_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_xd_, tmp_a_, tmp_ud_,
+                                                                                       1);
     k_vertex_third<R><<<grid_rows(), 256, 0, st>>>(d_, (R*)out);
+    d_.material = mat_;
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -348,21 +358,31 @@ class Engine final : public EngineBase {
 
   int grid_rows() const { return (L_.Np + 255) / 256; }
   size_t n3() const { return 3 * (size_t)L_.Np; }
-  R* sx(int j) const { return seg_x_ + n3() * j; }
-  R* sv(int j) const { return seg_v_ + n3() * j; }
+  double* sx(int j) const { return seg_x_ + n3() * j; }
+  double* sv(int j) const { return seg_v_ + n3() * j; }
 
-  void gather(const R* in, R* out, cudaStream_t st) { k_gather<R><<<grid_rows(), 256, 0, st>>>(d_, in, out); }
+  void gather(const R* in, R* out, cudaStream_t st) { k_gather<R, R, R><<<grid_rows(), 256, 0, st>>>(d_, in, out); }
+  void gather_state(const R* in, double* out, cudaStream_t st) {
+    k_gather<R, R, double><<<grid_rows(), 256, 0, st>>>(d_, in, out);
+  }
 
-  void elements(const R* x, cudaStream_t st) {
+  // single-stage entry points read their own material buffer
+  int use_material(const void* material, cudaStream_t st) {
+    CLOTH_CUDA(cudaMemcpyAsync(mat_tmp_, material, sizeof(R) * 4 * L_.S, cudaMemcpyDeviceToDevice, st));
+    d_.material = mat_tmp_;
+    return CLOTH_OK;
+  }
+
+  void elements(const double* x, cudaStream_t st) {
     if (L_.M) k_elem_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, x);
     if (L_.E) k_elem_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, x);
   }
 
   int assemble_at(const void* x, const void* v, const void* F, cudaStream_t st) {
-    gather((const R*)x, tmp_a_, st);
-    gather((const R*)v, tmp_b_, st);
-    elements(tmp_a_, st);
-    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, tmp_b_, (const R*)F);
+    gather_state((const R*)x, tmp_xd_, st);
+    gather_state((const R*)v, tmp_vd_, st);
+    elements(tmp_xd_, st);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, tmp_vd_, (const R*)F);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -419,7 +439,8 @@ class Engine final : public EngineBase {
   }
 
   // One implicit step from (x, v) to (xn, vn); F: user-layout force row or null.
-  int step(const R* x, const R* v, const R* F, R* xn, R* vn, R* traj_row, int phase, cudaStream_t st, bool cap) {
+  int step(const double* x, const double* v, const R* F, double* xn, double* vn, R* traj_row, int phase,
+           cudaStream_t st, bool cap) {
     elements(x, st);
     k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, v, F);
     CLOTH_CUDA(cudaGetLastError());
@@ -435,21 +456,21 @@ class Engine final : public EngineBase {
 
   int forward_body(const void* material, const void* x0, const void* v0, const void* forces, void* traj_x,
                    int32_t* status, cudaStream_t st, bool cap) {
-    (void)material;
     const size_t nu3 = 3 * (size_t)L_.Nu;
+    CLOTH_CUDA(cudaMemcpyAsync(mat_, material, sizeof(R) * 4 * L_.S, cudaMemcpyDeviceToDevice, st));
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
-    gather((const R*)x0, sx(0), st);
-    gather((const R*)v0, sv(0), st);
+    gather_state((const R*)x0, sx(0), st);
+    gather_state((const R*)v0, sv(0), st);
     CLOTH_CUDA(cudaMemcpyAsync(traj_x, x0, sizeof(R) * nu3, cudaMemcpyDeviceToDevice, st));
     for (int k = 0; k < nseg_; ++k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
       if (k > 0) {
-        CLOTH_CUDA(cudaMemcpyAsync(sx(0), sx(C_), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
-        CLOTH_CUDA(cudaMemcpyAsync(sv(0), sv(C_), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(sx(0), sx(C_), sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(sv(0), sv(C_), sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
       }
       if (nseg_ > 1) {
-        CLOTH_CUDA(cudaMemcpyAsync(ck_x_ + n3() * k, sx(0), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
-        CLOTH_CUDA(cudaMemcpyAsync(ck_v_ + n3() * k, sv(0), sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(ck_x_ + n3() * k, sx(0), sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(ck_v_ + n3() * k, sv(0), sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
       }
       for (int t = t0; t < t1; ++t) {
         const int j = t - t0;
@@ -474,8 +495,8 @@ class Engine final : public EngineBase {
     for (int k = nseg_ - 1; k >= 0; --k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
       if (k != seg_valid) {
-        CLOTH_CUDA(cudaMemcpyAsync(sx(0), ck_x_ + n3() * k, sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
-        CLOTH_CUDA(cudaMemcpyAsync(sv(0), ck_v_ + n3() * k, sizeof(R) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(sx(0), ck_x_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
+        CLOTH_CUDA(cudaMemcpyAsync(sv(0), ck_v_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
         for (int t = t0; t < t1; ++t) {
           const int j = t - t0;
           CLOTH_TRY(step(sx(j), sv(j), force_row(fwd_forces_, t), sx(j + 1), sv(j + 1), nullptr, kPhaseRecompute, st,
@@ -500,8 +521,8 @@ class Engine final : public EngineBase {
       }
     }
     if (g_material) k_grad_material<R><<<(L_.S + 127) / 128, 128, 0, st>>>(d_, (R*)g_material);
-    if (g_x0) k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, ax_, (R*)g_x0, R(1));
-    if (g_v0) k_scatter<R><<<grid_rows(), 256, 0, st>>>(d_, av_, (R*)g_v0, R(1));
+    if (g_x0) k_scatter<R, R><<<grid_rows(), 256, 0, st>>>(d_, ax_, (R*)g_x0);
+    if (g_v0) k_scatter<R, R><<<grid_rows(), 256, 0, st>>>(d_, av_, (R*)g_v0);
     k_status_out<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, status);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
@@ -544,14 +565,15 @@ class Engine final : public EngineBase {
   }
 
   BatchLayout L_;
-  const void* fwd_forces_ = nullptr;    // inputs of the last forward (the recompute reads them again)
-  const void* fwd_material_ = nullptr;
+  const void* fwd_forces_ = nullptr;  // force input of the last forward (the recompute reads it again)
   cloth_opts o_;
   Dev<R> d_;
   int T_ = 0, C_ = 0, nseg_ = 0, seg_valid_ = -1;
   bool have_forward_ = false;
-  R *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;
-  R *ax_ = nullptr, *av_ = nullptr, *tmp_a_ = nullptr, *tmp_b_ = nullptr, *tmp_c_ = nullptr;
+  double *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;
+  double *tmp_xd_ = nullptr, *tmp_vd_ = nullptr, *tmp_ud_ = nullptr;
+  R *ax_ = nullptr, *av_ = nullptr, *tmp_a_ = nullptr, *tmp_b_ = nullptr;
+  R *mat_ = nullptr, *mat_tmp_ = nullptr;
   double* lpart_ = nullptr;
   int* host_active_ = nullptr;
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;

@@ -214,6 +214,7 @@ class ClothBatch:
         self._t(forces, (T, N, 3), "forces")
         traj = self._new(T + 1, N, 3)
         status = torch.zeros(S, dtype=torch.int32, device="cuda")
+        self._fwd_forces = forces  # the backward's recompute reads it again
         _check(_lib.cloth_forward(self._h, _ptr(material), _ptr(x0), _ptr(v0), _ptr(forces), _ptr(traj),
                                   _ptr(status), self._stream()), "cloth_forward")
         return traj, status
