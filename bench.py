@@ -1,0 +1,457 @@
+"""Benchmark of the cloth step + adjoint (phi-SfT Sec. 3.1) on the GB300.
+
+One bench step = one full forward trajectory + trajectory loss + adjoint of every
+sheet of the workload (all hot-path stages: element kernels, assembly, Jacobi-PCG,
+state update, loss, adjoint solves and element adjoints, checkpoint recompute).
+Metric: vertex-steps/s = sum over sheets of (vertices x time steps) per bench step,
+divided by the device time of the step.
+
+Default workload: 256 sheets with grid sides uniform in [16, 64] vertices, materials
+sampled (Y log-uniform [1e2, 1e4] N/m, k_b log-uniform [1e-5, 1e-3] N m, rho uniform
+[0.05, 0.5] kg/m^2), 100 steps of 1/30 s, FP32, CG tol 1e-6, one captured CUDA graph
+per forward and per backward.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own batch (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_11938_gb300 import workloads as W  # noqa: E402
+
+METRIC = "vertex-steps/s fwd+adjoint, batched FP32 vs plain GPU at <=1e-3 grad err; HBM %"
+UNIT = "vertex-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129e6
+
+
+_T0 = time.time()
+
+
+def log(msg):
+    print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="batch256", choices=["batch256", "grid32", "grid100", "grid256"])
+    p.add_argument("--exec", dest="exec_mode", default="graph", choices=["graph", "plain"])
+    p.add_argument("--no-plain-baseline", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def make_workload(name, rank=0):
+    if name == "batch256":
+        return W.config4(seed=1 + rank)
+    if name == "grid32":
+        return W.config2()
+    if name == "grid100":
+        return W.config3()
+    return W.config5()
+
+
+def workload_config(wl, name):
+    sizes = [s.N for s in wl.sheets]
+    return {"workload": f"{name}: {len(sizes)} sheet(s), grid sides {min(sizes)}-{max(sizes)} "
+                        f"({wl.total_vertices} vertices), {wl.steps} steps dt={wl.dt:.5g}s, "
+                        f"{wl.precision}, CG tol {wl.cg_tol:g}, fwd+loss+adjoint",
+            "sheets": len(sizes), "vertices": wl.total_vertices, "time_steps": wl.steps,
+            "checkpoint_every": wl.checkpoint_every, "loss": wl.loss}
+
+
+def units_per_step(wl):
+    return wl.total_vertices * wl.steps
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except (ValueError, OSError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def committed_traffic(kernel="spmv"):
+    """Per-launch DRAM traffic of the SpMV kernel from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "cg_spmv_batch256.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch_full:"):
+            try:
+                return float(line.split(":", 1)[1].strip())
+            except ValueError:
+                return None
+    return None
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2203_11938_gb300 import build as _build
+
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist:
+        dist.barrier()
+    from paper_2203_11938_gb300 import sim
+
+    wl = make_workload(args.workload, rank)
+    log(f"workload {args.workload}: {len(wl.sheets)} sheets, {wl.total_vertices} vertices")
+    dtype = torch.float32 if wl.precision == "f32" else torch.float64
+    meshes = [(s.rest, s.tris, s.pinned) for s in wl.sheets]
+    b = sim.ClothBatch(meshes, steps=wl.steps, dt=wl.dt, precision=wl.precision, cg_tol=wl.cg_tol,
+                       cg_max_iter=wl.cg_max_iter, checkpoint_every=wl.checkpoint_every, exec_mode=args.exec_mode)
+    dev = "cuda"
+    mat = torch.tensor(np.stack([s.material for s in wl.sheets]), dtype=dtype, device=dev)
+    x0 = torch.tensor(np.concatenate([s.rest for s in wl.sheets]), dtype=dtype, device=dev)
+    v0 = torch.zeros_like(x0)
+    F = None
+    if wl.sheets[0].forces is not None:
+        F = torch.tensor(np.concatenate([s.forces for s in wl.sheets], axis=1), dtype=dtype, device=dev)
+    # target trajectory from scaled parameters (setup, not timed)
+    tgt_mat = mat * torch.tensor(wl.target_scale, dtype=dtype, device=dev)
+    log("batch created; target rollout")
+    target, _ = b.forward(tgt_mat, x0, v0, F)
+    target = target.clone()
+    torch.cuda.synchronize()
+    log("target done")
+    if wl.loss == "pinhole":
+        cam = wl.camera
+        Xc = target[..., 0] - cam[1]
+        Yc = -(target[..., 1] - cam[2])
+        Zc = cam[3] - target[..., 2]
+        target = torch.stack([cam[0] * Xc / Zc, cam[0] * Yc / Zc], dim=-1).contiguous()
+
+    def one_step():
+        traj, st = b.forward(mat, x0, v0, F)
+        if wl.loss == "pinhole":
+            loss, dL = b.loss_pinhole(traj, target, wl.camera)
+        else:
+            loss, dL = b.loss_l2(traj, target)
+        g = b.backward(dL, want=("material", "forces", "x0", "v0") if F is not None else ("material", "x0", "v0"))
+        return loss, g, st
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        loss, g, st = one_step()
+        torch.cuda.synchronize()
+        log(f"warm-up step done {b.stats()}")
+    stats = b.stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss, g, st = one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    log(f"timed region {ms:.1f} ms for {args.steps} steps")
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    stats = b.stats()
+    status = int(st.max().item()) | int(g["status"].max().item())
+    units = units_per_step(wl)
+    value = units * world * args.steps / (ms_max / 1e3)
+    launches_per_step = stats["kernel_launches"] + 2  # + the two loss kernels
+
+    # -------------------- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h_mat = mat.cpu().pin_memory()
+        h_x0 = x0.cpu().pin_memory()
+        h_v0 = v0.cpu().pin_memory()
+        h_tgt = target.cpu().pin_memory()
+        h_F = F.cpu().pin_memory() if F is not None else None
+        d_mat, d_x0, d_v0, d_tgt = torch.empty_like(mat), torch.empty_like(x0), torch.empty_like(v0), \
+            torch.empty_like(target)
+        d_F = torch.empty_like(F) if F is not None else None
+        out_loss = torch.empty(b.count, dtype=torch.float64).pin_memory()
+        out_g = torch.empty(b.count, 4, dtype=dtype).pin_memory()
+        bi = sum(t_.numel() * t_.element_size() for t_ in (h_mat, h_x0, h_v0, h_tgt) + ((h_F,) if h_F is not None else ()))
+        bo = out_loss.numel() * 8 + out_g.numel() * out_g.element_size()
+
+        def e2e_step():
+            d_mat.copy_(h_mat, non_blocking=True)
+            d_x0.copy_(h_x0, non_blocking=True)
+            d_v0.copy_(h_v0, non_blocking=True)
+            d_tgt.copy_(h_tgt, non_blocking=True)
+            if d_F is not None:
+                d_F.copy_(h_F, non_blocking=True)
+            traj, _ = b.forward(d_mat, d_x0, d_v0, d_F)
+            if wl.loss == "pinhole":
+                loss, dL = b.loss_pinhole(traj, d_tgt, wl.camera)
+            else:
+                loss, dL = b.loss_l2(traj, d_tgt)
+            gg = b.backward(dL, want=("material", "forces", "x0", "v0") if F is not None else ("material", "x0", "v0"))
+            out_loss.copy_(loss, non_blocking=True)
+            out_g.copy_(gg["material"], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = torch.tensor([a0.elapsed_time(a1)], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
+        e2e = {"value": units * world * args.e2e_steps / (float(ems.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+
+    log(f"e2e done {e2e}")
+    # -------------------- roofline of the dominant kernel (CG SpMV)
+    one_step()
+    torch.cuda.synchronize()
+    mi = b.matrix_info()
+    es = 4 if dtype == torch.float32 else 8
+    alg_bytes = mi["blocks"] * (9 * es + 4) + mi["rows"] * (2 * 3 * es)
+    spmv_ms = b.time_kernel("spmv", reps=50)
+    upd_ms = b.time_kernel("cg_update", reps=50)
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (spmv_ms / 1e3) / 1e9
+    traffic = committed_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (3x3-block SELL-32 SpMV + per-sheet FP64 p.Ap)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(spmv_ms, 5),
+                "bytes_per_vertex": round(alg_bytes / mi["rows"], 1),
+                "cg_update_ms": round(upd_ms, 5),
+                "cg_update_GBps": round(mi["rows"] * 3 * es * 7 / (upd_ms / 1e3) / 1e9, 1)}
+
+    log(f"roofline {roofline}")
+    # -------------------- plain single-sheet GPU path on a subset of the sheets
+    plain = None
+    if not args.no_plain_baseline and len(wl.sheets) > 1 and rank == 0:
+        sub = wl.sheets[:8]
+        tot_units, tot_ms = 0, 0.0
+        for s in sub:
+            bs = sim.ClothBatch([(s.rest, s.tris, s.pinned)], steps=wl.steps, dt=wl.dt, precision=wl.precision,
+                                cg_tol=wl.cg_tol, cg_max_iter=wl.cg_max_iter, exec_mode="plain")
+            m1 = torch.tensor(s.material[None], dtype=dtype, device=dev)
+            xs = torch.tensor(s.rest, dtype=dtype, device=dev)
+            vs = torch.zeros_like(xs)
+            tg, _ = bs.forward(m1 * torch.tensor(wl.target_scale, dtype=dtype, device=dev), xs, vs, None)
+            tg = tg.clone()
+            for rep in range(2):
+                torch.cuda.synchronize()
+                q0 = time.perf_counter()
+                tr, _ = bs.forward(m1, xs, vs, None)
+                _, dl = bs.loss_l2(tr, tg)
+                bs.backward(dl, want=("material", "x0", "v0"))
+                torch.cuda.synchronize()
+                q1 = time.perf_counter()
+            tot_units += s.n * wl.steps
+            tot_ms += (q1 - q0) * 1e3
+        plain = {"value": tot_units / (tot_ms / 1e3), "unit": UNIT, "sample": f"first {len(sub)} sheets, one "
+                 "sheet per call, host-polled CG (poll every 16 iterations), no graph"}
+
+    log(f"plain baseline {plain}")
+    # -------------------- CPU baseline (the oracle, bounded sample)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == torch.float32 else "f64",
+            "data": "synthetic (seeded grids shaped like the paper's sequences)",
+            "config": dict(workload_config(wl, args.workload),
+                           **{"l2": f"working set {b.workspace_bytes / 1e9:.2f} GB > 129 MB L2 (inputs larger than L2)",
+                              "exec": args.exec_mode}),
+            "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps), "roofline": roofline,
+            "cpu_baseline": cpu, "clocks": clocks,
+            "cg_iters_per_step": {"forward": stats["fwd_cg_iters"] / (wl.steps * len(wl.sheets)),
+                                  "adjoint": stats["bwd_cg_iters"] / (wl.steps * len(wl.sheets)),
+                                  "recompute": stats["recompute_cg_iters"] / (wl.steps * len(wl.sheets))},
+            "status_bits": status, "plain_single_sheet_gpu": plain,
+            "batched_vs_plain": (value / world) / plain["value"] if plain else None,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle
+def cpu_baseline(wl, budget_s=15.0):
+    """Time the FP64 oracle (as it stands) single-threaded on a bounded sample:
+    forward + trajectory loss + adjoint of the workload's first sheet for a few steps."""
+    import oracle
+
+    oracle.build()
+    s = wl.sheets[0]
+    o = oracle.OracleSim(s.rest, s.tris, s.pinned)
+    steps = 1
+    t_used, units = 0.0, 0
+    while True:
+        F = None if s.forces is None else s.forces[:steps]
+        q0 = time.perf_counter()
+        tx, tv, _, _ = o.forward(s.material, s.rest, np.zeros_like(s.rest), F, dt=wl.dt, steps=steps, tol=wl.cg_tol,
+                                 max_iter=wl.cg_max_iter, gravity=W.GRAVITY)
+        tgt = tx + 0.01
+        _, dL = oracle.loss_l2(tx, tgt)
+        o.backward(s.material, tx, tv, dL, dt=wl.dt, steps=steps, tol=wl.cg_tol, max_iter=wl.cg_max_iter,
+                   gravity=W.GRAVITY)
+        dt_ = time.perf_counter() - q0
+        t_used += dt_
+        units = s.n * steps
+        if dt_ >= budget_s / 3 or steps >= wl.steps or t_used > budget_s:
+            value = units / dt_
+            break
+        steps = min(wl.steps, max(steps + 1, int(steps * (budget_s / 3) / max(dt_, 1e-3))))
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"sheet 0 of the workload ({s.n} vertices), {steps} steps, FP64 forward + loss + adjoint, "
+                      f"single thread, {dt_:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    import oracle
+
+    oracle.build()
+    s = wl.sheets[0]
+    o = oracle.OracleSim(s.rest, s.tris, s.pinned)
+    steps = max(1, min(wl.steps, 3))
+
+    def one():
+        F = None if s.forces is None else s.forces[:steps]
+        tx, tv, _, _ = o.forward(s.material, s.rest, np.zeros_like(s.rest), F, dt=wl.dt, steps=steps, tol=wl.cg_tol,
+                                 max_iter=wl.cg_max_iter, gravity=W.GRAVITY)
+        _, dL = oracle.loss_l2(tx, tx + 0.01)
+        o.backward(s.material, tx, tv, dL, dt=wl.dt, steps=steps, tol=wl.cg_tol, max_iter=wl.cg_max_iter,
+                   gravity=W.GRAVITY)
+
+    for _ in range(args.warmup):
+        one()
+    q0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    sec = time.perf_counter() - q0
+    value = s.n * steps * args.steps / sec
+    sample = (f"sheet 0 of the workload ({s.n} vertices), {steps} steps per bench step, FP64 oracle forward + "
+              f"loss + adjoint, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(wl, args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

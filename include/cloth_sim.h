@@ -149,10 +149,25 @@ int cloth_loss_pinhole(cloth_batch* batch, const void* traj_x, const void* targe
                        const double* camera, double* loss, void* dL_dx, void* stream);
 
 /* CG iteration totals of the last forward and backward (summed over sheets and
- * steps; the backward's count includes its recomputed forward solves).
- * Synchronises the stream of the last call. Any pointer may be NULL. */
+ * steps; the backward's recomputed forward solves are counted apart), and the
+ * number of kernels the last forward plus backward launched, CG loop bodies
+ * included.  Synchronises the stream of the last call.  Any pointer may be NULL. */
 int cloth_stats(cloth_batch* batch, int64_t* fwd_cg_iters, int64_t* bwd_cg_iters,
-                int64_t* recompute_cg_iters);
+                int64_t* recompute_cg_iters, int64_t* kernel_launches);
+
+/* Size of the step matrix A (Eq. 4-5) in 3x3 blocks: rows (vertices, each sheet
+ * padded to a multiple of 32), blocks (structurally nonzero blocks) and
+ * stored_blocks (blocks stored by the SELL-32 layout, padding included). */
+int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks,
+                      int64_t* stored_blocks);
+
+/* Average device time [ms] of `reps` back-to-back launches of one step kernel on
+ * the state left by the last call, timed with CUDA events on `stream`:
+ * kernel 0 = CG SpMV with its per-sheet p^T A p reduction, 1 = CG vector update,
+ * 2 = assembly, 3 = membrane element kernel, 4 = bending element kernel.
+ * Needs a prior cloth_forward; synchronises `stream`. */
+int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* avg_ms,
+                      void* stream);
 
 /* ---- single-kernel entry points (parity checks of each stage) ---- */
 

@@ -149,9 +149,19 @@ int cloth_loss_pinhole(cloth_batch* batch, const void* traj_x, const void* targe
   return batch->engine->loss_pinhole(traj_x, target_uv, camera, loss, dL_dx, stream);
 }
 
-int cloth_stats(cloth_batch* batch, int64_t* fwd, int64_t* bwd, int64_t* rec) {
+int cloth_stats(cloth_batch* batch, int64_t* fwd, int64_t* bwd, int64_t* rec, int64_t* launches) {
   CLOTH_NEED_BATCH("cloth_stats");
-  return batch->engine->stats(fwd, bwd, rec);
+  return batch->engine->stats(fwd, bwd, rec, launches);
+}
+
+int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks, int64_t* stored_blocks) {
+  CLOTH_NEED_BATCH("cloth_matrix_info");
+  return batch->engine->matrix_info(rows, blocks, stored_blocks);
+}
+
+int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* avg_ms, void* stream) {
+  CLOTH_NEED_BATCH("cloth_time_kernel");
+  return batch->engine->time_kernel(kernel, reps, avg_ms, stream);
 }
 
 int cloth_internal_forces(cloth_batch* batch, const void* material, const void* x, void* f_membrane,

@@ -128,6 +128,13 @@ __device__ inline Sym2<T> stvk_stress(const TriConst<R>& k, const T F[3][2]) {
   return {R(2) * k.mu * g00 + ltr, R(2) * k.mu * g11 + ltr, R(2) * k.mu * g01};
 }
 
+// S = 2 mu G + lambda tr(G) I from a Green strain computed elsewhere
+template <class R>
+__device__ inline Sym2<R> stvk_stress_G(const TriConst<R>& k, Sym2<R> G) {
+  const R ltr = k.lam * (G.a + G.b);
+  return {R(2) * k.mu * G.a + ltr, R(2) * k.mu * G.b + ltr, R(2) * k.mu * G.c};
+}
+
 // C : X for symmetric X:  2 mu X + lambda tr(X) I
 template <class T, class R>
 __device__ inline Sym2<T> elastic_map(const TriConst<R>& k, Sym2<T> X) {
@@ -155,12 +162,15 @@ __device__ inline V3<T> mat32_sym_vec(const T A[3][2], Sym2<T> S, const R* g) {
 
 // Forces and upper Hessian blocks of one triangle.
 // f[3]: -dE/dx_a.  H[6][9]: blocks (0,0),(0,1),(0,2),(1,1),(1,2),(2,2), row-major 3x3.
-// clamp: geometric term uses S+ (eps = k.eps) instead of S.
+// G: the Green strain of the element (formed by the caller from edge metrics, so it
+// keeps its relative precision when the strain is small); clamp: the geometric term
+// uses S+ (eps = k.eps) instead of S.
 template <class R>
-__device__ inline void membrane_force_hessian(const TriConst<R>& k, const V3<R>* x, bool clamp, V3<R>* f, R (*H)[9]) {
+__device__ inline void membrane_force_hessian(const TriConst<R>& k, const V3<R>* x, Sym2<R> G, bool clamp, V3<R>* f,
+                                              R (*H)[9]) {
   R F[3][2];
   deformation_gradient(k, x, F);
-  Sym2<R> S = stvk_stress(k, F);
+  Sym2<R> S = stvk_stress_G(k, G);
   Sym2<R> Sg = clamp ? smooth_positive(S, k.eps) : S;
   V3<R> w[3];
   for (int a = 0; a < 3; ++a) {
@@ -204,14 +214,14 @@ __device__ inline void direction_gradient(const TriConst<R>& k, const V3<R>* u, 
 //   Hx_lam = H lam (exact Hessian),  Hc_lam = H~ lam,  Hc_u = H~ u,  f = -dE/dx,
 //   third = d/dx (lam^T H~(x) u).
 template <class R>
-__device__ inline void membrane_adjoint(const TriConst<R>& k, const V3<R>* x, const V3<R>* lam, const V3<R>* u,
-                                        bool clamp, V3<R>* f, V3<R>* Hx_lam, V3<R>* Hc_lam, V3<R>* Hc_u,
-                                        V3<R>* third) {
+__device__ inline void membrane_adjoint(const TriConst<R>& k, const V3<R>* x, Sym2<R> G, const V3<R>* lam,
+                                        const V3<R>* u, bool clamp, V3<R>* f, V3<R>* Hx_lam, V3<R>* Hc_lam,
+                                        V3<R>* Hc_u, V3<R>* third) {
   R F[3][2], dFl[3][2], dFu[3][2];
   deformation_gradient(k, x, F);
   direction_gradient(k, lam, dFl);
   direction_gradient(k, u, dFu);
-  Sym2<R> S = stvk_stress(k, F);
+  Sym2<R> S = stvk_stress_G(k, G);
   Sym2<R> Sg = clamp ? smooth_positive(S, k.eps) : S;
   Sym2<R> dGl = sym_FtdF(F, dFl), dGu = sym_FtdF(F, dFu);
   Sym2<R> dSl = elastic_map(k, dGl), dSu = elastic_map(k, dGu);

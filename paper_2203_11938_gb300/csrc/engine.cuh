@@ -42,6 +42,7 @@ struct Dev {
   int S, Np, Nu, M, E, nslices, NW;
   const int *tri_v, *tri_sheet;
   const R* tri_rest;
+  const double* tri_metric;  // [3][M] rest edge metric
   const int *hin_v, *hin_sheet;
   const R* hin_rest;
   const int *i2u, *u2i;
@@ -61,6 +62,7 @@ struct Dev {
   double* part;
   int* active;
   unsigned long long* iter_total;
+  unsigned long long* body_runs;  // [3] CG loop-body executions per phase
   double* gacc;  // [S][3] dL/dY, dL/dkb, dL/drho
   // parameters
   R h, gx, gy, gz, eta;
@@ -194,6 +196,40 @@ __device__ __forceinline__ void load_relative(const double* __restrict__ x, cons
   }
 }
 
+// out_a = sum_b H_ab v_b from the upper 3x3 blocks of a K-vertex element (H_ba = H_ab^T).
+template <class R, int K>
+__device__ __forceinline__ void block_matvec(const R (*H)[9], const V3<R>* v, V3<R>* out) {
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    R o[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      const int lo = a < b ? a : b, hi = a < b ? b : a;
+      const R* Hb = H[lo * K - lo * (lo - 1) / 2 + (hi - lo)];
+      const R vb[3] = {v[b].x, v[b].y, v[b].z};
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) o[c] += (a <= b ? Hb[3 * c + e] : Hb[3 * e + c]) * vb[e];
+    }
+    out[a] = {o[0], o[1], o[2]};
+  }
+}
+
+// Relative vectors of an element (u_a - u_0), differences formed in FP64: every
+// element operator here annihilates uniform translations, so dropping the common
+// part first removes the cancellation of large, nearly rigid motions.
+template <class R, int K>
+__device__ __forceinline__ void load_relative_dir(const R* __restrict__ u, const int* idx, V3<R>* out) {
+  const V3<R> u0 = ld3(u, idx[0]);
+  out[0] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int a = 1; a < K; ++a) {
+    const V3<R> ua = ld3(u, idx[a]);
+    out[a] = {(R)((double)ua.x - (double)u0.x), (R)((double)ua.y - (double)u0.y), (R)((double)ua.z - (double)u0.z)};
+  }
+}
+
 template <class R>
 __device__ __forceinline__ V3<R> ld3r(const double* __restrict__ x, int i) {
   const V3<double> v = ld3(x, i);
@@ -221,6 +257,28 @@ __device__ __forceinline__ TriConst<R> tri_const(const Dev<R>& d, int t) {
   return k;
 }
 
+// Green strain G = Bm^T (Ds^T Ds - Dm^T Dm) Bm / 2 with the edge metric difference
+// formed in FP64 from the FP64 state (no cancellation of the identity in F^T F - I).
+template <class R>
+__device__ __forceinline__ Sym2<R> green_strain(const Dev<R>& d, int t, const double* __restrict__ x,
+                                                const int* idx) {
+  const V3<double> x0 = ld3(x, idx[0]), x1 = ld3(x, idx[1]), x2 = ld3(x, idx[2]);
+  const V3<double> e1 = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
+  const V3<double> e2 = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
+  const double m00 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z - d.tri_metric[t];
+  const double m11 = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z - d.tri_metric[(size_t)d.M + t];
+  const double m01 = e1.x * e2.x + e1.y * e2.y + e1.z * e2.z - d.tri_metric[2 * (size_t)d.M + t];
+  const double b00 = d.tri_rest[t], b01 = d.tri_rest[(size_t)d.M + t];
+  const double b10 = d.tri_rest[2 * (size_t)d.M + t], b11 = d.tri_rest[3 * (size_t)d.M + t];
+  // (dM Bm) then Bm^T (dM Bm)
+  const double q00 = m00 * b00 + m01 * b10, q01 = m00 * b01 + m01 * b11;
+  const double q10 = m01 * b00 + m11 * b10, q11 = m01 * b01 + m11 * b11;
+  const double g00 = 0.5 * (b00 * q00 + b10 * q10);
+  const double g11 = 0.5 * (b01 * q01 + b11 * q11);
+  const double g01 = 0.5 * (b00 * q01 + b10 * q11);
+  return {(R)g00, (R)g11, (R)g01};
+}
+
 template <class R>
 __device__ __forceinline__ HingeConst<R> hinge_const(const Dev<R>& d, int e) {
   const int s = d.hin_sheet[e];
@@ -228,7 +286,8 @@ __device__ __forceinline__ HingeConst<R> hinge_const(const Dev<R>& d, int e) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const double* __restrict__ x) {
+__global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const double* __restrict__ x,
+                                                          const double* __restrict__ v) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.M) return;
   TriConst<R> k = tri_const(d, t);
@@ -238,7 +297,14 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const doubl
 #pragma unroll
   for (int a = 0; a < 3; ++a) idx[a] = d.tri_v[(size_t)a * d.M + t];
   load_relative<R, 3>(x, idx, xe);
-  membrane_force_hessian(k, xe, d.clamp, f, H);
+  membrane_force_hessian(k, xe, green_strain(d, t, x, idx), d.clamp, f, H);
+  if (v) {  // store f - h H~ v (the element's share of b / h)
+    V3<R> ve[3], Hv[3];
+    load_relative<R, 3>(v, idx, ve);
+    block_matvec<R, 3>(H, ve, Hv);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = {f[a].x - d.h * Hv[a].x, f[a].y - d.h * Hv[a].y, f[a].z - d.h * Hv[a].z};
+  }
   R* fo = d.tri_f + 9 * (size_t)t;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -254,7 +320,8 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const doubl
 }
 
 template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const double* __restrict__ x) {
+__global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const double* __restrict__ x,
+                                                            const double* __restrict__ v) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   HingeConst<R> k = hinge_const(d, e);
@@ -265,6 +332,13 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const dou
   for (int a = 0; a < 4; ++a) idx[a] = d.hin_v[(size_t)a * d.E + e];
   load_relative<R, 4>(x, idx, xe);
   bending_force_hessian(k, xe, f, H);
+  if (v) {
+    V3<R> ve[4], Hv[4];
+    load_relative<R, 4>(v, idx, ve);
+    block_matvec<R, 4>(H, ve, Hv);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) f[a] = {f[a].x - d.h * Hv[a].x, f[a].y - d.h * Hv[a].y, f[a].z - d.h * Hv[a].z};
+  }
   R* fo = d.hin_f + 12 * (size_t)e;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -308,9 +382,11 @@ __device__ __forceinline__ void gather_block(const Dev<R>& d, int ent, R (&Hb)[9
 }
 
 // Assembly of A, b, D^{-1} (one thread per row; a warp is one SELL slice).
+// The element kernels stored f_e - h H~_e v_e per element vertex, so
+// b_i = h (sum_e (f_e - h H~_e v_e)_i + m_i g + F_i)  (= h (f + M g + F) - h^2 H~ v).
 // Fext: user-layout external force of this step or null.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const double* __restrict__ v, const R* __restrict__ Fext) {
+__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __restrict__ Fext) {
   const int w = blockIdx.x;
   const int s = d.work_sheet[w];
   if (threadIdx.x >= d.work_rows[w]) return;
@@ -328,17 +404,12 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const double* _
     f.y += src[1];
     f.z += src[2];
   }
-  V3<R> Hv = {R(0), R(0), R(0)};
   R diag[3] = {R(1), R(1), R(1)};
   for (int k = 0; k < K; ++k) {
     const int ent = (base + k) * 32 + lane;
     const int j = d.cols[ent];
     R Hb[9];
     gather_block(d, ent, Hb);
-    const V3<R> vj = ld3r<R>(v, j);
-    Hv.x += Hb[0] * vj.x + Hb[1] * vj.y + Hb[2] * vj.z;
-    Hv.y += Hb[3] * vj.x + Hb[4] * vj.y + Hb[5] * vj.z;
-    Hv.z += Hb[6] * vj.x + Hb[7] * vj.y + Hb[8] * vj.z;
     const bool zero = pin_i || d.pinned[j] != 0;
     R* dst = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
 #pragma unroll
@@ -355,9 +426,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const double* _
   if (!pin_i) {
     const int u = d.i2u[i];
     V3<R> fe = Fext && u >= 0 ? ld3(Fext, u) : V3<R>{R(0), R(0), R(0)};
-    b.x = h * (f.x + mass * d.gx + fe.x) - h2 * Hv.x;
-    b.y = h * (f.y + mass * d.gy + fe.y) - h2 * Hv.y;
-    b.z = h * (f.z + mass * d.gz + fe.z) - h2 * Hv.z;
+    b.x = h * (f.x + mass * d.gx + fe.x);
+    b.y = h * (f.y + mass * d.gy + fe.y);
+    b.z = h * (f.z + mass * d.gz + fe.z);
   }
   st3(d.bvec, i, b);
   st3(d.dinv, i, V3<R>{R(1) / diag[0], R(1) / diag[1], R(1) / diag[2]});
@@ -492,10 +563,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cud
   }
 }
 
-// p = D^{-1} r + beta p
+// p = D^{-1} r + beta p  (also counts the loop-body executions of this phase)
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
+__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d, int phase) {
   const int w = blockIdx.x, s = d.work_sheet[w];
+  if (w == 0 && threadIdx.x == 0) d.body_runs[phase] += 1ull;
   if (d.cg[s].done) return;
   if (threadIdx.x >= d.work_rows[w]) return;
   const int i = d.work_row0[w] + threadIdx.x;
@@ -525,7 +597,17 @@ template <class R>
 __global__ void k_reset_status(Dev<R> d, int phase) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < d.S) d.cg[s].status = 0;
-  if (s == 0) d.iter_total[phase] = 0;
+  if (s == 0) {
+    d.iter_total[phase] = 0;
+    d.body_runs[phase] = 0;
+  }
+}
+
+// Re-open every sheet's CG (kernel timing on the last assembled system).
+template <class R>
+__global__ void k_reopen(Dev<R> d) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < d.S) d.cg[s].done = 0;
 }
 
 template <class R>
@@ -546,13 +628,11 @@ __global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const double
   V3<R> xe[3], le[3], ue[3], f[3], Hx[3], Hl[3], Hu[3], th[3];
   int idx[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    idx[a] = d.tri_v[(size_t)a * d.M + t];
-    le[a] = ld3(lam, idx[a]);
-    ue[a] = ld3r<R>(u, idx[a]);
-  }
+  for (int a = 0; a < 3; ++a) idx[a] = d.tri_v[(size_t)a * d.M + t];
   load_relative<R, 3>(x, idx, xe);
-  membrane_adjoint(k, xe, le, ue, d.clamp, f, Hx, Hl, Hu, th);
+  load_relative_dir<R, 3>(lam, idx, le);
+  load_relative<R, 3>(u, idx, ue);
+  membrane_adjoint(k, xe, green_strain(d, t, x, idx), le, ue, d.clamp, f, Hx, Hl, Hu, th);
   const R h = d.h, h2 = d.h * d.h;
   R* ro = d.tri_r + 18 * (size_t)t;
   double sc = 0.0;
@@ -590,12 +670,10 @@ __global__ void __launch_bounds__(kElemThreads) k_adj_hinge(Dev<R> d, const doub
   V3<R> xe[4], le[4], ue[4], f[4], Hl[4], Hu[4], th[4];
   int idx[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    idx[a] = d.hin_v[(size_t)a * d.E + e];
-    le[a] = ld3(lam, idx[a]);
-    ue[a] = ld3r<R>(u, idx[a]);
-  }
+  for (int a = 0; a < 4; ++a) idx[a] = d.hin_v[(size_t)a * d.E + e];
   load_relative<R, 4>(x, idx, xe);
+  load_relative_dir<R, 4>(lam, idx, le);
+  load_relative<R, 4>(u, idx, ue);
   bending_adjoint(k, xe, le, ue, f, Hl, Hu, th);
   const R h = d.h, h2 = d.h * d.h;
   R* ro = d.hin_r + 24 * (size_t)e;

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "engine.cuh"
@@ -27,6 +28,14 @@ namespace cloth {
 
 template <class R>
 class Engine final : public EngineBase {
+  // Every host-issued kernel launch goes through here so the launch count of a call
+  // is known (CG loop-body kernels are counted on the device instead).
+  template <class... P, class... A>
+  void launch(void (*kern)(P...), dim3 g, dim3 b, cudaStream_t st, A&&... args) {
+    kern<<<g, b, 0, st>>>(std::forward<A>(args)...);
+    ++launches_;
+  }
+
  public:
   Engine(const BatchLayout& L, const cloth_opts& o) : L_(L), o_(o) {}
 
@@ -36,6 +45,8 @@ class Engine final : public EngineBase {
     if (cap_stream_) cudaStreamDestroy(cap_stream_);
     if (body_stream_) cudaStreamDestroy(body_stream_);
     if (host_active_) cudaFreeHost(host_active_);
+    if (ev0_) cudaEventDestroy(ev0_);
+    if (ev1_) cudaEventDestroy(ev1_);
     for (void* p : allocs_) cudaFree(p);
   }
 
@@ -69,6 +80,7 @@ class Engine final : public EngineBase {
     d.tri_v = up_i(L_.tri_v);
     d.tri_sheet = up_i(L_.tri_sheet);
     d.tri_rest = up_r(L_.tri_rest);
+    d.tri_metric = upload(L_.tri_metric, &rc);
     d.hin_v = up_i(L_.hin_v);
     d.hin_sheet = up_i(L_.hin_sheet);
     d.hin_rest = up_r(L_.hin_rest);
@@ -116,6 +128,7 @@ class Engine final : public EngineBase {
     d.part = alloc<double>(2 * (size_t)d.NW, &rc);
     d.active = alloc<int>(1, &rc);
     d.iter_total = alloc<unsigned long long>(3, &rc);
+    d.body_runs = alloc<unsigned long long>(3, &rc);
     d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
     // the state (x, v) is carried in FP64 in both precisions
     seg_x_ = alloc<double>(n3 * (C_ + 1), &rc);
@@ -142,6 +155,8 @@ class Engine final : public EngineBase {
     if (cudaMemset(d.cnt, 0, sizeof(int) * L_.S) != cudaSuccess ||
         cudaMemset(d.cg, 0, sizeof(CGSheet) * L_.S) != cudaSuccess ||
         cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
+        cudaMemset(d.body_runs, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
+        cudaEventCreate(&ev0_) != cudaSuccess || cudaEventCreate(&ev1_) != cudaSuccess ||
         cudaMallocHost(&host_active_, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&body_stream_, cudaStreamNonBlocking) != cudaSuccess) {
@@ -168,12 +183,15 @@ class Engine final : public EngineBase {
     fwd_forces_ = forces;
     if (o_.exec == CLOTH_EXEC_GRAPH) {
       GraphKey key{0, {material, x0, v0, forces, traj_x, status, nullptr, nullptr, nullptr, nullptr}, 0};
-      CLOTH_TRY(run_graph(key, st, [&](cudaStream_t s) {
+      CLOTH_TRY(run_graph(key, st, &fixed_fwd_, [&](cudaStream_t s) {
         return forward_body(material, x0, v0, forces, traj_x, status, s, true);
       }));
     } else {
+      launches_ = 0;
       CLOTH_TRY(forward_body(material, x0, v0, forces, traj_x, status, st, false));
+      fixed_fwd_ = launches_;
     }
+    fixed_bwd_ = 0;
     have_forward_ = true;
     seg_valid_ = nseg_ - 1;
     return CLOTH_OK;
@@ -196,23 +214,75 @@ class Engine final : public EngineBase {
     if (o_.exec == CLOTH_EXEC_GRAPH) {
       GraphKey key{1, {fwd_forces_, dL_dx, g_material, g_forces, g_x0, g_v0, status, nullptr, nullptr, nullptr},
                    seg_valid};
-      CLOTH_TRY(run_graph(key, st, [&](cudaStream_t s) {
+      CLOTH_TRY(run_graph(key, st, &fixed_bwd_, [&](cudaStream_t s) {
         return backward_body(dL_dx, g_material, g_forces, g_x0, g_v0, status, s, true, seg_valid);
       }));
     } else {
+      launches_ = 0;
       CLOTH_TRY(backward_body(dL_dx, g_material, g_forces, g_x0, g_v0, status, st, false, seg_valid));
+      fixed_bwd_ = launches_;
     }
     seg_valid_ = 0;
     return CLOTH_OK;
   }
 
-  int stats(int64_t* fwd, int64_t* bwd, int64_t* rec) override {
+  int stats(int64_t* fwd, int64_t* bwd, int64_t* rec, int64_t* launches) override {
     CLOTH_CUDA(cudaStreamSynchronize(last_stream_));
-    unsigned long long h[3];
+    unsigned long long h[3], b[3];
     CLOTH_CUDA(cudaMemcpy(h, d_.iter_total, sizeof(h), cudaMemcpyDeviceToHost));
+    CLOTH_CUDA(cudaMemcpy(b, d_.body_runs, sizeof(b), cudaMemcpyDeviceToHost));
     if (fwd) *fwd = (int64_t)h[0];
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
+    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + 3 * (int64_t)(b[0] + b[1] + b[2]);
+    return CLOTH_OK;
+  }
+
+  int matrix_info(int64_t* rows, int64_t* blocks, int64_t* slots) override {
+    if (rows) *rows = L_.Np;
+    if (blocks) {
+      int64_t nb = 0;
+      for (size_t i = 0; i + 1 < L_.contrib_ptr.size(); ++i) nb += L_.contrib_ptr[i + 1] > L_.contrib_ptr[i] ? 1 : 0;
+      // rows without element blocks (padding) still hold their identity diagonal
+      for (int i = 0; i < L_.Np; ++i) nb += L_.i2u[i] < 0 ? 1 : 0;
+      *blocks = nb;
+    }
+    if (slots) *slots = (int64_t)L_.total_slots() * 32;
+    return CLOTH_OK;
+  }
+
+  // Average duration of `reps` back-to-back launches of one step kernel on the
+  // system left by the last call (0: CG SpMV with its per-sheet p^T A p reduction,
+  // 1: CG vector update, 2: assembly, 3: membrane element kernel, 4: bending element
+  // kernel), timed with CUDA events on `stream`.
+  int time_kernel(int which, int reps, double* avg_ms, void* stream_) override {
+    if (!have_forward_ || reps < 1 || !avg_ms) return invalid("cloth_time_kernel: needs a forward and reps >= 1");
+    cudaStream_t st = (cudaStream_t)stream_;
+    d_.material = mat_;
+    const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
+    auto one = [&]() {
+      switch (which) {
+        case 0: k_cg_spmv<R><<<d_.NW, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
+        case 1: k_cg_update<R><<<d_.NW, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
+        case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr); break;
+        case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
+        default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
+      }
+    };
+    if (which < 0 || which > 4) return invalid("cloth_time_kernel: unknown kernel id");
+    k_reopen<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_);
+    one();  // warm-up
+    k_reopen<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_);
+    CLOTH_CUDA(cudaEventRecord(ev0_, st));
+    for (int k = 0; k < reps; ++k) one();
+    CLOTH_CUDA(cudaEventRecord(ev1_, st));
+    CLOTH_CUDA(cudaEventSynchronize(ev1_));
+    float ms = 0.f;
+    CLOTH_CUDA(cudaEventElapsedTime(&ms, ev0_, ev1_));
+    *avg_ms = ms / reps;
+    // leave the CG state closed again
+    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
+    CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
 
@@ -253,7 +323,7 @@ class Engine final : public EngineBase {
     cudaStream_t st = (cudaStream_t)stream_;
     CLOTH_TRY(use_material(material, st));
     gather_state((const R*)x, tmp_xd_, st);
-    elements(tmp_xd_, st);
+    elements(tmp_xd_, nullptr, st);
     if (fm) k_vertex_force<R><<<grid_rows(), 256, 0, st>>>(d_, 0, (R*)fm);
     if (fb) k_vertex_force<R><<<grid_rows(), 256, 0, st>>>(d_, 1, (R*)fb);
     d_.material = mat_;
@@ -329,6 +399,7 @@ class Engine final : public EngineBase {
   struct CachedGraph {
     GraphKey key;
     cudaGraphExec_t exec = nullptr;
+    int64_t fixed = 0;  // host-issued kernel nodes (CG loop bodies excluded)
   };
 
   int invalid(const char* msg) {
@@ -361,9 +432,9 @@ class Engine final : public EngineBase {
   double* sx(int j) const { return seg_x_ + n3() * j; }
   double* sv(int j) const { return seg_v_ + n3() * j; }
 
-  void gather(const R* in, R* out, cudaStream_t st) { k_gather<R, R, R><<<grid_rows(), 256, 0, st>>>(d_, in, out); }
+  void gather(const R* in, R* out, cudaStream_t st) { launch(k_gather<R, R, R>, dim3(grid_rows()), dim3(256), st, d_, in, out); }
   void gather_state(const R* in, double* out, cudaStream_t st) {
-    k_gather<R, R, double><<<grid_rows(), 256, 0, st>>>(d_, in, out);
+    launch(k_gather<R, R, double>, dim3(grid_rows()), dim3(256), st, d_, in, out);
   }
 
   // single-stage entry points read their own material buffer
@@ -373,16 +444,19 @@ class Engine final : public EngineBase {
     return CLOTH_OK;
   }
 
-  void elements(const double* x, cudaStream_t st) {
-    if (L_.M) k_elem_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, x);
-    if (L_.E) k_elem_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, x);
+  // element forces and Hessian blocks at x; with v, the stored element vectors are f - h H~ v
+  void elements(const double* x, const double* v, cudaStream_t st) {
+    if (L_.M)
+      launch(k_elem_tri<R>, dim3((L_.M + kElemThreads - 1) / kElemThreads), dim3(kElemThreads), st, d_, x, v);
+    if (L_.E)
+      launch(k_elem_hinge<R>, dim3((L_.E + kElemThreads - 1) / kElemThreads), dim3(kElemThreads), st, d_, x, v);
   }
 
   int assemble_at(const void* x, const void* v, const void* F, cudaStream_t st) {
     gather_state((const R*)x, tmp_xd_, st);
     gather_state((const R*)v, tmp_vd_, st);
-    elements(tmp_xd_, st);
-    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, tmp_vd_, (const R*)F);
+    elements(tmp_xd_, tmp_vd_, st);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, (const R*)F);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -390,8 +464,8 @@ class Engine final : public EngineBase {
   // Solve A y = rhs (y left in d_.dv) for every sheet.  In graph mode the CG loop is a
   // conditional WHILE node whose condition the kernels clear when the last sheet ends.
   int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
-    k_solve_begin<R><<<1, 32, 0, st>>>(d_);
-    k_cg_init<R><<<d_.NW, kThreads, 0, st>>>(d_, rhs, phase);
+    launch(k_solve_begin<R>, dim3(1), dim3(32), st, d_);
+    launch(k_cg_init<R>, dim3(d_.NW), dim3(kThreads), st, d_, rhs, phase);
     CLOTH_CUDA(cudaGetLastError());
     if (capturing) {
       cudaStreamCaptureStatus cs;
@@ -401,7 +475,7 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
       cudaGraphConditionalHandle cond;
       CLOTH_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
-      k_cond_set<R><<<1, 32, 0, st>>>(d_, cond);
+      launch(k_cond_set<R>, dim3(1), dim3(32), st, d_, cond);
       CLOTH_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
       cudaGraphNodeParams cp = {};
       cp.type = cudaGraphNodeTypeConditional;
@@ -415,7 +489,7 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       k_cg_spmv<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
       k_cg_update<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
-      k_cg_dir<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_);
+      k_cg_dir<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase);
       cudaGraph_t out = nullptr;
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
@@ -430,7 +504,7 @@ class Engine final : public EngineBase {
       for (int k = 0; k < poll; ++k) {
         k_cg_spmv<R><<<d_.NW, kThreads, 0, st>>>(d_, phase, 0, 0);
         k_cg_update<R><<<d_.NW, kThreads, 0, st>>>(d_, phase, 0, 0);
-        k_cg_dir<R><<<d_.NW, kThreads, 0, st>>>(d_);
+        k_cg_dir<R><<<d_.NW, kThreads, 0, st>>>(d_, phase);
       }
       launched += poll;
       CLOTH_CUDA(cudaGetLastError());
@@ -441,11 +515,11 @@ class Engine final : public EngineBase {
   // One implicit step from (x, v) to (xn, vn); F: user-layout force row or null.
   int step(const double* x, const double* v, const R* F, double* xn, double* vn, R* traj_row, int phase,
            cudaStream_t st, bool cap) {
-    elements(x, st);
-    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, v, F);
+    elements(x, v, st);
+    launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, F);
     CLOTH_CUDA(cudaGetLastError());
     CLOTH_TRY(solve(d_.bvec, phase, st, cap));
-    k_state_update<R><<<grid_rows(), 256, 0, st>>>(d_, x, v, xn, vn, traj_row);
+    launch(k_state_update<R>, dim3(grid_rows()), dim3(256), st, d_, x, v, xn, vn, traj_row);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -458,7 +532,7 @@ class Engine final : public EngineBase {
                    int32_t* status, cudaStream_t st, bool cap) {
     const size_t nu3 = 3 * (size_t)L_.Nu;
     CLOTH_CUDA(cudaMemcpyAsync(mat_, material, sizeof(R) * 4 * L_.S, cudaMemcpyDeviceToDevice, st));
-    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
+    launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseForward);
     gather_state((const R*)x0, sx(0), st);
     gather_state((const R*)v0, sv(0), st);
     CLOTH_CUDA(cudaMemcpyAsync(traj_x, x0, sizeof(R) * nu3, cudaMemcpyDeviceToDevice, st));
@@ -478,7 +552,7 @@ class Engine final : public EngineBase {
         CLOTH_TRY(step(sx(j), sv(j), force_row(forces, t), sx(j + 1), sv(j + 1), row, kPhaseForward, st, cap));
       }
     }
-    k_status_out<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, status);
+    launch(k_status_out<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, status);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -486,15 +560,17 @@ class Engine final : public EngineBase {
   int backward_body(const void* dL_dx, void* g_material, void* g_forces, void* g_x0, void* g_v0, int32_t* status,
                     cudaStream_t st, bool cap, int seg_valid) {
     const size_t nu3 = 3 * (size_t)L_.Nu;
-    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseBackward);
-    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseRecompute);
+    launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseBackward);
+    launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseRecompute);
     CLOTH_CUDA(cudaMemsetAsync(d_.gacc, 0, sizeof(double) * 3 * L_.S, st));
     gather((const R*)dL_dx + (size_t)T_ * nu3, ax_, st);
     CLOTH_CUDA(cudaMemsetAsync(av_, 0, sizeof(R) * n3(), st));
     const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
     for (int k = nseg_ - 1; k >= 0; --k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
-      if (k != seg_valid) {
+      // The segment buffer still holds segment k only if it is the first one swept
+      // (the last segment of the forward); any other segment is recomputed.
+      if (!(k == nseg_ - 1 && seg_valid == nseg_ - 1)) {
         CLOTH_CUDA(cudaMemcpyAsync(sx(0), ck_x_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
         CLOTH_CUDA(cudaMemcpyAsync(sv(0), ck_v_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
         for (int t = t0; t < t1; ++t) {
@@ -506,38 +582,41 @@ class Engine final : public EngineBase {
       for (int t = t1 - 1; t >= t0; --t) {
         const int j = t - t0;
         // A_t at x_t (the RHS of the step matrix is not needed)
-        elements(sx(j), st);
-        k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, sv(j), nullptr);
-        k_adj_rhs<R><<<grid_rows(), 256, 0, st>>>(d_, ax_, av_);
+        elements(sx(j), nullptr, st);
+        launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, (const R*)nullptr);
+        launch(k_adj_rhs<R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)ax_, (const R*)av_);
         CLOTH_CUDA(cudaGetLastError());
         CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap));
-        if (L_.M) k_adj_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(j), d_.dv, sv(j + 1), 0);
-        if (L_.E) k_adj_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(j), d_.dv, sv(j + 1), 0);
+        if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const R*)d_.dv, (const double*)sv(j + 1), 0);
+        if (L_.E) launch(k_adj_hinge<R>, dim3(ge), dim3(kElemThreads), st, d_, (const double*)sx(j), (const R*)d_.dv, (const double*)sv(j + 1), 0);
         R* gF = g_forces ? (R*)g_forces + (size_t)t * nu3 : nullptr;
-        k_adj_vertex<R><<<grid_rows(), 256, 0, st>>>(d_, ax_, av_, sv(j), sv(j + 1), (const R*)dL_dx + (size_t)t * nu3,
-                                                     gF);
-        k_param_acc<R><<<L_.S, kThreads, 0, st>>>(d_);
+        launch(k_adj_vertex<R>, dim3(grid_rows()), dim3(256), st, d_, ax_, av_, (const double*)sv(j), (const double*)sv(j + 1),
+               (const R*)dL_dx + (size_t)t * nu3, gF);
+        launch(k_param_acc<R>, dim3(L_.S), dim3(kThreads), st, d_);
         CLOTH_CUDA(cudaGetLastError());
       }
     }
-    if (g_material) k_grad_material<R><<<(L_.S + 127) / 128, 128, 0, st>>>(d_, (R*)g_material);
-    if (g_x0) k_scatter<R, R><<<grid_rows(), 256, 0, st>>>(d_, ax_, (R*)g_x0);
-    if (g_v0) k_scatter<R, R><<<grid_rows(), 256, 0, st>>>(d_, av_, (R*)g_v0);
-    k_status_out<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, status);
+    if (g_material) launch(k_grad_material<R>, dim3((L_.S + 127) / 128), dim3(128), st, d_, (R*)g_material);
+    if (g_x0) launch(k_scatter<R, R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)ax_, (R*)g_x0);
+    if (g_v0) launch(k_scatter<R, R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)av_, (R*)g_v0);
+    launch(k_status_out<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, status);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
 
   // Capture `body` into a graph once per argument set, then launch it on `st`.
   template <class Body>
-  int run_graph(const GraphKey& key, cudaStream_t st, Body body) {
+  int run_graph(const GraphKey& key, cudaStream_t st, int64_t* fixed, Body body) {
     for (auto& g : graphs_)
       if (g.key == key) {
+        *fixed = g.fixed;
         CLOTH_CUDA(cudaGraphLaunch(g.exec, st));
         return CLOTH_OK;
       }
+    launches_ = 0;
     CLOTH_CUDA(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeRelaxed));
     int rc = body(cap_stream_);
+    *fixed = launches_;
     cudaGraph_t graph = nullptr;
     cudaError_t ec = cudaStreamEndCapture(cap_stream_, &graph);
     if (rc != CLOTH_OK) {
@@ -559,7 +638,7 @@ class Engine final : public EngineBase {
       cudaGraphExecDestroy(graphs_.front().exec);
       graphs_.erase(graphs_.begin());
     }
-    graphs_.push_back({key, exec});
+    graphs_.push_back({key, exec, *fixed});
     CLOTH_CUDA(cudaGraphLaunch(exec, st));
     return CLOTH_OK;
   }
@@ -578,6 +657,8 @@ class Engine final : public EngineBase {
   int* host_active_ = nullptr;
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;
   std::vector<CachedGraph> graphs_;
+  int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
+  cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
   std::vector<void*> allocs_;
   size_t bytes_ = 0;
 };

@@ -102,6 +102,7 @@ int build_mesh(const double* rest, int n, const int* tris, int m, const uint8_t*
       return CLOTH_ERR_INVALID_ARG;
     }
   d.tri_rest.resize(5 * (size_t)m);
+  d.tri_metric.resize(3 * (size_t)m);
   d.area3.assign(n, 0.0);
   for (int t = 0; t < m; ++t) {
     const int* v = &tris[3 * t];
@@ -116,6 +117,14 @@ int build_mesh(const double* rest, int n, const int* tris, int m, const uint8_t*
       return CLOTH_ERR_DEGENERATE;
     }
     for (int a = 0; a < 3; ++a) d.area3[v[a]] += d.tri_rest[5 * (size_t)t + 4] / 3.0;
+    double E1[3], E2[3];
+    for (int c = 0; c < 3; ++c) {
+      E1[c] = rest[3 * v[1] + c] - rest[3 * v[0] + c];
+      E2[c] = rest[3 * v[2] + c] - rest[3 * v[0] + c];
+    }
+    d.tri_metric[3 * (size_t)t] = E1[0] * E1[0] + E1[1] * E1[1] + E1[2] * E1[2];
+    d.tri_metric[3 * (size_t)t + 1] = E2[0] * E2[0] + E2[1] * E2[1] + E2[2] * E2[2];
+    d.tri_metric[3 * (size_t)t + 2] = E1[0] * E2[0] + E1[1] * E2[1] + E1[2] * E2[2];
   }
   // Interior edges: sort the 3m half-edges by undirected key; a run of two is a hinge.
   std::vector<HalfEdge> he;
@@ -190,6 +199,7 @@ void build_layout(const std::vector<const MeshData*>& sheets, BatchLayout* Lp) {
   L.tri_v.assign(3 * (size_t)L.M, 0);
   L.tri_sheet.assign(L.M, 0);
   L.tri_rest.assign(5 * (size_t)L.M, 0.0);
+  L.tri_metric.assign(3 * (size_t)L.M, 0.0);
   L.hin_v.assign(4 * (size_t)L.E, 0);
   L.hin_sheet.assign(L.E, 0);
   L.hin_rest.assign(2 * (size_t)L.E, 0.0);
@@ -249,6 +259,7 @@ void build_layout(const std::vector<const MeshData*>& sheets, BatchLayout* Lp) {
     for (int t = 0; t < d.m; ++t) {
       for (int a = 0; a < 3; ++a) L.tri_v[(size_t)a * L.M + toff + t] = loc2int[d.tris[3 * t + a]];
       for (int q = 0; q < 5; ++q) L.tri_rest[(size_t)q * L.M + toff + t] = d.tri_rest[5 * (size_t)t + q];
+      for (int q = 0; q < 3; ++q) L.tri_metric[(size_t)q * L.M + toff + t] = d.tri_metric[3 * (size_t)t + q];
       L.tri_sheet[toff + t] = s;
     }
     for (int e = 0; e < ne; ++e) {

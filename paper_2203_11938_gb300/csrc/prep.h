@@ -21,6 +21,7 @@ struct MeshData {
   std::vector<uint8_t> pinned;     // [n]
   std::vector<int> hinges;         // [e][4]: edge (e0, e1), wing of the first triangle, wing of the second
   std::vector<double> tri_rest;    // [m][5]: Dm^{-1} row-major (4), rest area A0
+  std::vector<double> tri_metric;  // [m][3]: rest metric E1.E1, E2.E2, E1.E2 of the edges E1 = X1-X0, E2 = X2-X0
   std::vector<double> hinge_rest;  // [e][2]: w_e = 3|e|^2/(A1+A2), rest dihedral angle
   std::vector<double> area3;       // [n]: sum over incident triangles of A0/3 (mass per unit density)
   int num_hinges() const { return (int)hinges.size() / 4; }
@@ -50,6 +51,7 @@ struct BatchLayout {
   std::vector<int> tri_v;          // [3][M]
   std::vector<int> tri_sheet;      // [M]
   std::vector<double> tri_rest;    // [5][M]
+  std::vector<double> tri_metric;  // [3][M]
   std::vector<int> hin_v;          // [4][E]
   std::vector<int> hin_sheet;      // [E]
   std::vector<double> hin_rest;    // [2][E]

@@ -31,7 +31,7 @@ EXPORTS = (
     "cloth_default_opts", "cloth_mesh_create", "cloth_mesh_destroy", "cloth_mesh_info", "cloth_batch_create",
     "cloth_batch_destroy", "cloth_batch_info", "cloth_forward", "cloth_backward", "cloth_loss_l2",
     "cloth_loss_pinhole", "cloth_stats", "cloth_internal_forces", "cloth_system_dense", "cloth_spmv",
-    "cloth_third_contraction", "cloth_last_error",
+    "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel",
 )
 
 
@@ -78,7 +78,9 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_backward.argtypes = [_vp] * 8
     lib.cloth_loss_l2.argtypes = [_vp] * 6
     lib.cloth_loss_pinhole.argtypes = [_vp] * 7
-    lib.cloth_stats.argtypes = [_vp] * 4
+    lib.cloth_stats.argtypes = [_vp] * 5
+    lib.cloth_matrix_info.argtypes = [_vp] * 4
+    lib.cloth_time_kernel.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.cloth_internal_forces.argtypes = [_vp] * 6
     lib.cloth_system_dense.argtypes = [_vp] * 8
     lib.cloth_spmv.argtypes = [_vp] * 7
@@ -262,9 +264,25 @@ class ClothBatch:
         return loss, grad
 
     def stats(self):
-        f, b, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(_lib.cloth_stats(self._h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(r)), "cloth_stats")
-        return {"fwd_cg_iters": f.value, "bwd_cg_iters": b.value, "recompute_cg_iters": r.value}
+        f, b, r, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.cloth_stats(self._h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(r), ctypes.byref(n)),
+               "cloth_stats")
+        return {"fwd_cg_iters": f.value, "bwd_cg_iters": b.value, "recompute_cg_iters": r.value,
+                "kernel_launches": n.value}
+
+    def matrix_info(self):
+        r, b, s = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.cloth_matrix_info(self._h, ctypes.byref(r), ctypes.byref(b), ctypes.byref(s)),
+               "cloth_matrix_info")
+        return {"rows": r.value, "blocks": b.value, "stored_blocks": s.value}
+
+    KERNELS = {"spmv": 0, "cg_update": 1, "assemble": 2, "elem_tri": 3, "elem_hinge": 4}
+
+    def time_kernel(self, name, reps=20):
+        ms = ctypes.c_double()
+        _check(_lib.cloth_time_kernel(self._h, self.KERNELS[name], int(reps), ctypes.byref(ms), self._stream()),
+               "cloth_time_kernel")
+        return ms.value
 
     def internal_forces(self, material, x):
         N, S = self.total_vertices, self.count
