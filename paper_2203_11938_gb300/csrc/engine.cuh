@@ -42,9 +42,11 @@ struct Dev {
   int S, Np, Nu, M, E, nslices, NW;
   const int *tri_v, *tri_sheet;
   const R* tri_rest;
+  const double* tri_rest_d;  // [5][M] the same rest data in FP64 (force path)
   const double* tri_metric;  // [3][M] rest edge metric
   const int *hin_v, *hin_sheet;
   const R* hin_rest;
+  const double* hin_rest_d;  // [2][E] FP64 copy (force path)
   const int *i2u, *u2i;
   const uint8_t* pinned;
   const R* area3;
@@ -54,7 +56,8 @@ struct Dev {
   const int *work_sheet, *work_row0, *work_rows, *sheet_wfirst;
   const int *sheet_uoff, *sheet_voff, *sheet_toff, *sheet_hoff;
   // scratch
-  R *tri_f, *tri_H, *hin_f, *hin_H, *tri_r, *hin_r;
+  double *tri_f, *hin_f;  // element force vectors f_e - h H~_e v_e, FP64
+  R *tri_H, *hin_H, *tri_r, *hin_r;
   double *tri_sc, *hin_sc, *row_sc;
   R *Aval, *bvec, *dinv, *r, *p, *Ap, *dv;
   CGSheet* cg;
@@ -285,6 +288,64 @@ __device__ __forceinline__ HingeConst<R> hinge_const(const Dev<R>& d, int e) {
   return {d.material[4 * s + 2] * d.hin_rest[e], d.hin_rest[(size_t)d.E + e]};
 }
 
+// Membrane force -dE/dx_a = -A0 F S g_a in FP64.  Element forces of a tensioned sheet
+// are tens to hundreds of times larger than the net force per vertex, so they are
+// formed and summed in FP64 whatever the batch precision (the Hessian stays in R).
+template <class R>
+__device__ __forceinline__ void membrane_force_fp64(const Dev<R>& d, int t, const V3<double>* xr, V3<double>* f) {
+  TriConst<double> k;
+  const double b00 = d.tri_rest_d[t], b01 = d.tri_rest_d[(size_t)d.M + t];
+  const double b10 = d.tri_rest_d[2 * (size_t)d.M + t], b11 = d.tri_rest_d[3 * (size_t)d.M + t];
+  k.g[1][0] = b00;
+  k.g[1][1] = b01;
+  k.g[2][0] = b10;
+  k.g[2][1] = b11;
+  k.g[0][0] = -(b00 + b10);
+  k.g[0][1] = -(b01 + b11);
+  k.A0 = d.tri_rest_d[4 * (size_t)d.M + t];
+  const int s = d.tri_sheet[t];
+  const double Y = (double)d.material[4 * s], nu = (double)d.material[4 * s + 1];
+  k.mu = Y / (2.0 * (1.0 + nu));
+  k.lam = Y * nu / (1.0 - nu * nu);
+  k.eps = 0.0;
+  // G from the edge metric difference (exact zero at rest)
+  const V3<double> e1 = xr[1], e2 = xr[2];
+  const double m00 = dot(e1, e1) - d.tri_metric[t];
+  const double m11 = dot(e2, e2) - d.tri_metric[(size_t)d.M + t];
+  const double m01 = dot(e1, e2) - d.tri_metric[2 * (size_t)d.M + t];
+  const double q00 = m00 * b00 + m01 * b10, q01 = m00 * b01 + m01 * b11;
+  const double q10 = m01 * b00 + m11 * b10, q11 = m01 * b01 + m11 * b11;
+  const Sym2<double> G = {0.5 * (b00 * q00 + b10 * q10), 0.5 * (b01 * q01 + b11 * q11), 0.5 * (b00 * q01 + b10 * q11)};
+  double F[3][2];
+  deformation_gradient(k, xr, F);
+  const Sym2<double> S = stvk_stress_G(k, G);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) f[a] = scale(-k.A0, mat32_sym_vec(F, S, k.g[a]));
+}
+
+template <class R>
+__device__ __forceinline__ void bending_force_fp64(const Dev<R>& d, int e, const V3<double>* xr, V3<double>* f) {
+  const int s = d.hin_sheet[e];
+  const double kw = (double)d.material[4 * s + 2] * d.hin_rest_d[e];
+  double th;
+  V3<double> g[4];
+  dihedral_grad(xr, th, g);
+  const double c = -kw * (th - d.hin_rest_d[(size_t)d.E + e]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) f[a] = scale(c, g[a]);
+}
+
+template <class R, int K>
+__device__ __forceinline__ void load_relative_d(const double* __restrict__ x, const int* idx, V3<double>* out) {
+  const V3<double> x0 = ld3(x, idx[0]);
+  out[0] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 1; a < K; ++a) {
+    const V3<double> xa = ld3(x, idx[a]);
+    out[a] = {xa.x - x0.x, xa.y - x0.y, xa.z - x0.z};
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const double* __restrict__ x,
                                                           const double* __restrict__ v) {
@@ -298,19 +359,23 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const doubl
   for (int a = 0; a < 3; ++a) idx[a] = d.tri_v[(size_t)a * d.M + t];
   load_relative<R, 3>(x, idx, xe);
   membrane_force_hessian(k, xe, green_strain(d, t, x, idx), d.clamp, f, H);
+  V3<double> xr[3], fd[3];
+  load_relative_d<R, 3>(x, idx, xr);
+  membrane_force_fp64(d, t, xr, fd);
   if (v) {  // store f - h H~ v (the element's share of b / h)
     V3<R> ve[3], Hv[3];
     load_relative<R, 3>(v, idx, ve);
     block_matvec<R, 3>(H, ve, Hv);
+    const double h = (double)d.h;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) f[a] = {f[a].x - d.h * Hv[a].x, f[a].y - d.h * Hv[a].y, f[a].z - d.h * Hv[a].z};
+    for (int a = 0; a < 3; ++a) fd[a] = {fd[a].x - h * Hv[a].x, fd[a].y - h * Hv[a].y, fd[a].z - h * Hv[a].z};
   }
-  R* fo = d.tri_f + 9 * (size_t)t;
+  double* fo = d.tri_f + 9 * (size_t)t;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    fo[3 * a] = f[a].x;
-    fo[3 * a + 1] = f[a].y;
-    fo[3 * a + 2] = f[a].z;
+    fo[3 * a] = fd[a].x;
+    fo[3 * a + 1] = fd[a].y;
+    fo[3 * a + 2] = fd[a].z;
   }
   R* ho = d.tri_H + 54 * (size_t)t;
 #pragma unroll
@@ -332,19 +397,23 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const dou
   for (int a = 0; a < 4; ++a) idx[a] = d.hin_v[(size_t)a * d.E + e];
   load_relative<R, 4>(x, idx, xe);
   bending_force_hessian(k, xe, f, H);
+  V3<double> xr[4], fd[4];
+  load_relative_d<R, 4>(x, idx, xr);
+  bending_force_fp64(d, e, xr, fd);
   if (v) {
     V3<R> ve[4], Hv[4];
     load_relative<R, 4>(v, idx, ve);
     block_matvec<R, 4>(H, ve, Hv);
+    const double h = (double)d.h;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) f[a] = {f[a].x - d.h * Hv[a].x, f[a].y - d.h * Hv[a].y, f[a].z - d.h * Hv[a].z};
+    for (int a = 0; a < 4; ++a) fd[a] = {fd[a].x - h * Hv[a].x, fd[a].y - h * Hv[a].y, fd[a].z - h * Hv[a].z};
   }
-  R* fo = d.hin_f + 12 * (size_t)e;
+  double* fo = d.hin_f + 12 * (size_t)e;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    fo[3 * a] = f[a].x;
-    fo[3 * a + 1] = f[a].y;
-    fo[3 * a + 2] = f[a].z;
+    fo[3 * a] = fd[a].x;
+    fo[3 * a + 1] = fd[a].y;
+    fo[3 * a + 2] = fd[a].z;
   }
   R* ho = d.hin_H + 90 * (size_t)e;
 #pragma unroll
@@ -355,7 +424,7 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const dou
 
 // element-vertex force slot -> pointer to 3 reals
 template <class R>
-__device__ __forceinline__ const R* force_slot(const Dev<R>& d, int slot) {
+__device__ __forceinline__ const double* force_slot(const Dev<R>& d, int slot) {
   return slot < 3 * d.M ? d.tri_f + 3 * (size_t)slot : d.hin_f + 3 * (size_t)(slot - 3 * d.M);
 }
 
@@ -396,10 +465,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
   const bool pin_i = d.pinned[i] != 0;
   const R rho = d.material[4 * s + 3];
   const R mass = rho * d.area3[i];
-  const R h = d.h, h2 = d.h * d.h;
-  V3<R> f = {R(0), R(0), R(0)};
+  const R h2 = d.h * d.h;
+  V3<double> f = {0.0, 0.0, 0.0};
   for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
-    const R* src = force_slot(d, d.vf[q]);
+    const double* src = force_slot(d, d.vf[q]);
     f.x += src[0];
     f.y += src[1];
     f.z += src[2];
@@ -426,9 +495,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
   if (!pin_i) {
     const int u = d.i2u[i];
     V3<R> fe = Fext && u >= 0 ? ld3(Fext, u) : V3<R>{R(0), R(0), R(0)};
-    b.x = h * (f.x + mass * d.gx + fe.x);
-    b.y = h * (f.y + mass * d.gy + fe.y);
-    b.z = h * (f.z + mass * d.gz + fe.z);
+    const double h = (double)d.h, md = (double)mass;
+    b.x = (R)(h * (f.x + md * (double)d.gx + (double)fe.x));
+    b.y = (R)(h * (f.y + md * (double)d.gy + (double)fe.y));
+    b.z = (R)(h * (f.z + md * (double)d.gz + (double)fe.z));
   }
   st3(d.bvec, i, b);
   st3(d.dinv, i, V3<R>{R(1) / diag[0], R(1) / diag[1], R(1) / diag[2]});
@@ -780,14 +850,14 @@ __global__ void k_vertex_force(Dev<R> d, int kind, R* __restrict__ out) {
   if (i >= d.Np) return;
   const int u = d.i2u[i];
   if (u < 0) return;
-  V3<R> f = {R(0), R(0), R(0)};
+  V3<double> f = {0.0, 0.0, 0.0};
   for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
     const int slot = d.vf[q];
     if ((slot < 3 * d.M) != (kind == 0)) continue;
-    const R* src = force_slot(d, slot);
-    f = add3(f, V3<R>{src[0], src[1], src[2]});
+    const double* src = force_slot(d, slot);
+    f = add3(f, V3<double>{src[0], src[1], src[2]});
   }
-  st3(out, u, f);
+  st3(out, u, V3<R>{(R)f.x, (R)f.y, (R)f.z});
 }
 
 template <class R>

@@ -80,10 +80,12 @@ class Engine final : public EngineBase {
     d.tri_v = up_i(L_.tri_v);
     d.tri_sheet = up_i(L_.tri_sheet);
     d.tri_rest = up_r(L_.tri_rest);
+    d.tri_rest_d = upload(L_.tri_rest, &rc);
     d.tri_metric = upload(L_.tri_metric, &rc);
     d.hin_v = up_i(L_.hin_v);
     d.hin_sheet = up_i(L_.hin_sheet);
     d.hin_rest = up_r(L_.hin_rest);
+    d.hin_rest_d = upload(L_.hin_rest, &rc);
     d.i2u = up_i(L_.i2u);
     d.u2i = up_i(L_.u2i);
     d.pinned = upload(L_.pinned, &rc);
@@ -107,9 +109,9 @@ class Engine final : public EngineBase {
     d.sheet_hoff = up_i(L_.sheet_hoff);
     const size_t n3 = 3 * (size_t)L_.Np;
     const size_t M = L_.M, E = L_.E;
-    d.tri_f = alloc<R>(9 * M, &rc);
+    d.tri_f = alloc<double>(9 * M, &rc);
     d.tri_H = alloc<R>(54 * M, &rc);
-    d.hin_f = alloc<R>(12 * E, &rc);
+    d.hin_f = alloc<double>(12 * E, &rc);
     d.hin_H = alloc<R>(90 * E, &rc);
     d.tri_r = alloc<R>(18 * M, &rc);
     d.hin_r = alloc<R>(24 * E, &rc);
