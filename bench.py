@@ -57,17 +57,28 @@ def parse():
     p.add_argument("--no-plain-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--time-steps", type=int, default=0,
+                   help="override the workload's time-step count (profiling runs; not a bench value)")
     return p.parse_args()
 
 
-def make_workload(name, rank=0):
+def make_workload(name, rank=0, steps=0):
     if name == "batch256":
-        return W.config4(seed=1 + rank)
-    if name == "grid32":
-        return W.config2()
-    if name == "grid100":
-        return W.config3()
-    return W.config5()
+        wl = W.config4(seed=1 + rank)
+    elif name == "grid32":
+        wl = W.config2()
+    elif name == "grid100":
+        wl = W.config3()
+    else:
+        wl = W.config5()
+    if steps:
+        wl.steps = steps
+        for s in wl.sheets:
+            if s.forces is not None:
+                s.forces = s.forces[:steps]
+        if wl.checkpoint_every >= steps:
+            wl.checkpoint_every = 0
+    return wl
 
 
 def workload_config(wl, name):
@@ -182,7 +193,7 @@ def run_ours(args):
         dist.barrier()
     from paper_2203_11938_gb300 import sim
 
-    wl = make_workload(args.workload, rank)
+    wl = make_workload(args.workload, rank, args.time_steps)
     log(f"workload {args.workload}: {len(wl.sheets)} sheets, {wl.total_vertices} vertices")
     dtype = torch.float32 if wl.precision == "f32" else torch.float64
     meshes = [(s.rest, s.tris, s.pinned) for s in wl.sheets]
@@ -302,6 +313,8 @@ def run_ours(args):
 
     log(f"e2e done {e2e}")
     # -------------------- roofline of the dominant kernel (CG SpMV)
+    if args.steps == 0:
+        return
     one_step()
     torch.cuda.synchronize()
     mi = b.matrix_info()
@@ -411,7 +424,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, 0, args.time_steps)
     import oracle
 
     oracle.build()

@@ -59,7 +59,8 @@ struct Dev {
   double *tri_f, *hin_f;  // element force vectors f_e - h H~_e v_e, FP64
   R *tri_H, *hin_H, *tri_r, *hin_r;
   double *tri_sc, *hin_sc, *row_sc;
-  R *Aval, *bvec, *dinv, *r, *p, *Ap, *dv;
+  R *Aval, *bvec, *dinv, *r, *p, *Ap;
+  double* dv;  // CG solution (dv, or lambda in the adjoint), accumulated in FP64
   CGSheet* cg;
   int* cnt;
   double* part;
@@ -473,22 +474,40 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
     f.y += src[1];
     f.z += src[2];
   }
+  // Slot 0 stores the row sum R_i = sum_j A_ij instead of A_ii, which the SpMV uses in
+  // difference form (A p)_i = R_i p_i + sum_{j != i} A_ij (p_j - p_i).  H annihilates
+  // uniform translations, so R_i = m_i I - h^2 sum_{pinned j} H_ij exactly (no
+  // cancellation), and smooth p no longer cancels large terms in the product.
   R diag[3] = {R(1), R(1), R(1)};
+  R rsum[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) rsum[q] = R(0);
   for (int k = 0; k < K; ++k) {
     const int ent = (base + k) * 32 + lane;
     const int j = d.cols[ent];
     R Hb[9];
     gather_block(d, ent, Hb);
-    const bool zero = pin_i || d.pinned[j] != 0;
+    const bool pin_j = d.pinned[j] != 0;
+    const bool zero = pin_i || pin_j;
     R* dst = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
+    if (k == 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) diag[q] = pin_i ? R(1) : mass + h2 * Hb[4 * q];
+      continue;  // written after the loop
+    }
+    if (!pin_i && pin_j && j != i) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) rsum[q] += Hb[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dst[q * 32] = zero ? R(0) : h2 * Hb[q];
+  }
+  {
+    R* dst = d.Aval + (size_t)base * 32 * 9 + lane;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      R a = zero ? R(0) : h2 * Hb[q];
-      if (k == 0 && (q == 0 || q == 4 || q == 8)) {
-        a += pin_i ? R(1) : mass;
-        diag[q / 4] = a;
-      }
-      dst[q * 32] = a;
+      const R dq = (q == 0 || q == 4 || q == 8) ? (pin_i ? R(1) : mass) : R(0);
+      dst[q * 32] = pin_i ? dq : dq - h2 * rsum[q];
     }
   }
   V3<R> b = {R(0), R(0), R(0)};
@@ -528,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
     const V3<R> z = {di.x * r.x, di.y * r.y, di.z * r.z};
     st3(d.r, i, r);
     st3(d.p, i, z);
-    st3(d.dv, i, V3<R>{R(0), R(0), R(0)});
+    st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
     v[0] = ddot3(r, z);
     v[1] = ddot3(r, r);
   }
@@ -563,18 +582,22 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
   if (on) {
     const int sl = i >> 5, lane = i & 31;
     const int K = d.slice_K[sl], base = d.slice_base[sl];
-    V3<R> y = {R(0), R(0), R(0)};
-    for (int k = 0; k < K; ++k) {
+    const V3<R> pi = ld3(d.p, i);
+    const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
+    V3<R> y = {a0[0] * pi.x + a0[32] * pi.y + a0[64] * pi.z, a0[96] * pi.x + a0[128] * pi.y + a0[160] * pi.z,
+               a0[192] * pi.x + a0[224] * pi.y + a0[256] * pi.z};
+    for (int k = 1; k < K; ++k) {
       const int ent = (base + k) * 32 + lane;
       const int j = d.cols[ent];
       const R* a = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
       const V3<R> pj = ld3(d.p, j);
-      y.x += a[0] * pj.x + a[32] * pj.y + a[64] * pj.z;
-      y.y += a[96] * pj.x + a[128] * pj.y + a[160] * pj.z;
-      y.z += a[192] * pj.x + a[224] * pj.y + a[256] * pj.z;
+      const V3<R> dp = {pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
+      y.x += a[0] * dp.x + a[32] * dp.y + a[64] * dp.z;
+      y.y += a[96] * dp.x + a[128] * dp.y + a[160] * dp.z;
+      y.z += a[192] * dp.x + a[224] * dp.y + a[256] * dp.z;
     }
     st3(d.Ap, i, y);
-    v[0] = ddot3(ld3(d.p, i), y);
+    v[0] = ddot3(pi, y);
   }
   double tot[1];
   if (sheet_reduce<1>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
@@ -604,8 +627,10 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cud
   double v[2] = {0.0, 0.0};
   if (on) {
     const V3<R> p = ld3(d.p, i), Ap = ld3(d.Ap, i);
-    V3<R> x = ld3(d.dv, i), r = ld3(d.r, i);
-    x = axpy3(alpha, p, x);
+    V3<double> x = ld3(d.dv, i);
+    V3<R> r = ld3(d.r, i);
+    const double al = d.cg[s].alpha;
+    x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
     r = axpy3(-alpha, Ap, r);
     st3(d.dv, i, x);
     st3(d.r, i, r);
@@ -652,9 +677,9 @@ __global__ void k_state_update(Dev<R> d, const double* __restrict__ x, const dou
                                double* __restrict__ xn, double* __restrict__ vn, R* __restrict__ traj_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
-  const V3<R> dv = ld3(d.dv, i);
+  const V3<double> dv = ld3(d.dv, i);
   const V3<double> v0 = ld3(v, i), x0 = ld3(x, i);
-  const V3<double> v1 = {v0.x + (double)dv.x, v0.y + (double)dv.y, v0.z + (double)dv.z};
+  const V3<double> v1 = {v0.x + dv.x, v0.y + dv.y, v0.z + dv.z};
   const double h = (double)d.h;
   const V3<double> x1 = {x0.x + h * v1.x, x0.y + h * v1.y, x0.z + h * v1.z};
   st3(vn, i, v1);
@@ -690,8 +715,8 @@ __global__ void k_status_out(Dev<R> d, int32_t* status) {
 // mode 0: adjoint step contributions; mode 1: third-derivative contraction only.
 template <class R>
 __global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const double* __restrict__ x,
-                                                         const R* __restrict__ lam, const double* __restrict__ u,
-                                                         int mode) {
+                                                         const double* __restrict__ lam,
+                                                         const double* __restrict__ u, int mode) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.M) return;
   TriConst<R> k = tri_const(d, t);
@@ -700,7 +725,7 @@ __global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const double
 #pragma unroll
   for (int a = 0; a < 3; ++a) idx[a] = d.tri_v[(size_t)a * d.M + t];
   load_relative<R, 3>(x, idx, xe);
-  load_relative_dir<R, 3>(lam, idx, le);
+  load_relative<R, 3>(lam, idx, le);
   load_relative<R, 3>(u, idx, ue);
   membrane_adjoint(k, xe, green_strain(d, t, x, idx), le, ue, d.clamp, f, Hx, Hl, Hu, th);
   const R h = d.h, h2 = d.h * d.h;
@@ -732,8 +757,8 @@ __global__ void __launch_bounds__(kElemThreads) k_adj_tri(Dev<R> d, const double
 
 template <class R>
 __global__ void __launch_bounds__(kElemThreads) k_adj_hinge(Dev<R> d, const double* __restrict__ x,
-                                                           const R* __restrict__ lam, const double* __restrict__ u,
-                                                           int mode) {
+                                                           const double* __restrict__ lam,
+                                                           const double* __restrict__ u, int mode) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   HingeConst<R> k = hinge_const(d, e);
@@ -742,7 +767,7 @@ __global__ void __launch_bounds__(kElemThreads) k_adj_hinge(Dev<R> d, const doub
 #pragma unroll
   for (int a = 0; a < 4; ++a) idx[a] = d.hin_v[(size_t)a * d.E + e];
   load_relative<R, 4>(x, idx, xe);
-  load_relative_dir<R, 4>(lam, idx, le);
+  load_relative<R, 4>(lam, idx, le);
   load_relative<R, 4>(u, idx, ue);
   bending_adjoint(k, xe, le, ue, f, Hl, Hu, th);
   const R h = d.h, h2 = d.h * d.h;
@@ -804,7 +829,7 @@ __global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, c
     r2.z += src[5];
   }
   const int u = d.i2u[i];
-  const V3<R> a_x = ld3(ax, i), a_v = ld3(av, i), lam = ld3(d.dv, i);
+  const V3<R> a_x = ld3(ax, i), a_v = ld3(av, i), lam = ld3r<R>(d.dv, i);
   const V3<R> dl = (dLdx_row && u >= 0) ? ld3(dLdx_row, u) : V3<R>{R(0), R(0), R(0)};
   st3(ax, i, V3<R>{a_x.x + r1.x + dl.x, a_x.y + r1.y + dl.y, a_x.z + r1.z + dl.z});
   st3(av, i, V3<R>{a_v.x + d.h * a_x.x + r2.x, a_v.y + d.h * a_x.y + r2.y, a_v.z + d.h * a_x.z + r2.z});
@@ -885,18 +910,24 @@ __global__ void k_dense(Dev<R> d, const long long* __restrict__ dense_off, R* __
   const int n = d.sheet_uoff[s + 1] - d.sheet_uoff[s];
   const int ul = u - d.sheet_uoff[s];
   const int sl = i >> 5, lane = i & 31;
-  for (int k = 0; k < d.slice_K[sl]; ++k) {
+  double diag[9];
+  {
+    const R* a0 = d.Aval + (size_t)d.slice_base[sl] * 32 * 9 + lane;
+    for (int q = 0; q < 9; ++q) diag[q] = (double)a0[q * 32];
+  }
+  for (int k = 1; k < d.slice_K[sl]; ++k) {
     const int ent = (d.slice_base[sl] + k) * 32 + lane;
     const int j = d.cols[ent];
     const int uj = d.i2u[j];
-    if (uj < 0) continue;
-    if (k > 0 && j == i) continue;  // padding slot
+    if (uj < 0 || j == i) continue;  // padding slot
     const int ujl = uj - d.sheet_uoff[s];
     const R* a = d.Aval + (size_t)(d.slice_base[sl] + k) * 32 * 9 + lane;
-    for (int c = 0; c < 3; ++c)
-      for (int e = 0; e < 3; ++e)
-        A[dense_off[s] + (size_t)(3 * ul + c) * (3 * n) + 3 * ujl + e] = a[(3 * c + e) * 32];
+    for (int q = 0; q < 9; ++q) {
+      diag[q] -= (double)a[q * 32];
+      A[dense_off[s] + (size_t)(3 * ul + q / 3) * (3 * n) + 3 * ujl + q % 3] = a[q * 32];
+    }
   }
+  for (int q = 0; q < 9; ++q) A[dense_off[s] + (size_t)(3 * ul + q / 3) * (3 * n) + 3 * ul + q % 3] = (R)diag[q];
 }
 
 // y = A p outside CG (for the single-kernel entry point)
@@ -905,14 +936,18 @@ __global__ void k_spmv_plain(Dev<R> d, const R* __restrict__ p, R* __restrict__ 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   const int sl = i >> 5, lane = i & 31;
-  V3<R> acc = {R(0), R(0), R(0)};
-  for (int k = 0; k < d.slice_K[sl]; ++k) {
+  const V3<R> pi = ld3(p, i);
+  const R* a0 = d.Aval + (size_t)d.slice_base[sl] * 32 * 9 + lane;
+  V3<R> acc = {a0[0] * pi.x + a0[32] * pi.y + a0[64] * pi.z, a0[96] * pi.x + a0[128] * pi.y + a0[160] * pi.z,
+               a0[192] * pi.x + a0[224] * pi.y + a0[256] * pi.z};
+  for (int k = 1; k < d.slice_K[sl]; ++k) {
     const int ent = (d.slice_base[sl] + k) * 32 + lane;
     const R* a = d.Aval + (size_t)(d.slice_base[sl] + k) * 32 * 9 + lane;
     const V3<R> pj = ld3(p, d.cols[ent]);
-    acc.x += a[0] * pj.x + a[32] * pj.y + a[64] * pj.z;
-    acc.y += a[96] * pj.x + a[128] * pj.y + a[160] * pj.z;
-    acc.z += a[192] * pj.x + a[224] * pj.y + a[256] * pj.z;
+    const V3<R> dp = {pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
+    acc.x += a[0] * dp.x + a[32] * dp.y + a[64] * dp.z;
+    acc.y += a[96] * dp.x + a[128] * dp.y + a[160] * dp.z;
+    acc.z += a[192] * dp.x + a[224] * dp.y + a[256] * dp.z;
   }
   st3(y, i, acc);
 }

@@ -124,7 +124,7 @@ class Engine final : public EngineBase {
     d.r = alloc<R>(n3, &rc);
     d.p = alloc<R>(n3, &rc);
     d.Ap = alloc<R>(n3, &rc);
-    d.dv = alloc<R>(n3, &rc);
+    d.dv = alloc<double>(n3, &rc);
     d.cg = alloc<CGSheet>(L_.S, &rc);
     d.cnt = alloc<int>(L_.S, &rc);
     d.part = alloc<double>(2 * (size_t)d.NW, &rc);
@@ -374,11 +374,11 @@ class Engine final : public EngineBase {
     cudaStream_t st = (cudaStream_t)stream_;
     CLOTH_TRY(use_material(material, st));
     gather_state((const R*)x, tmp_xd_, st);
-    gather((const R*)a, tmp_a_, st);
+    gather_state((const R*)a, tmp_vd_, st);
     gather_state((const R*)b, tmp_ud_, st);
-    k_adj_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_xd_, tmp_a_, tmp_ud_, 1);
+    k_adj_tri<R><<<(L_.M + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_xd_, tmp_vd_, tmp_ud_, 1);
     if (L_.E)
-      k_adj_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_xd_, tmp_a_, tmp_ud_,
+      k_adj_hinge<R><<<(L_.E + kElemThreads - 1) / kElemThreads, kElemThreads, 0, st>>>(d_, tmp_xd_, tmp_vd_, tmp_ud_,
                                                                                        1);
     k_vertex_third<R><<<grid_rows(), 256, 0, st>>>(d_, (R*)out);
     d_.material = mat_;
@@ -589,8 +589,8 @@ class Engine final : public EngineBase {
         launch(k_adj_rhs<R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)ax_, (const R*)av_);
         CLOTH_CUDA(cudaGetLastError());
         CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap));
-        if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const R*)d_.dv, (const double*)sv(j + 1), 0);
-        if (L_.E) launch(k_adj_hinge<R>, dim3(ge), dim3(kElemThreads), st, d_, (const double*)sx(j), (const R*)d_.dv, (const double*)sv(j + 1), 0);
+        if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
+        if (L_.E) launch(k_adj_hinge<R>, dim3(ge), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         R* gF = g_forces ? (R*)g_forces + (size_t)t * nu3 : nullptr;
         launch(k_adj_vertex<R>, dim3(grid_rows()), dim3(256), st, d_, ax_, av_, (const double*)sv(j), (const double*)sv(j + 1),
                (const R*)dL_dx + (size_t)t * nu3, gF);

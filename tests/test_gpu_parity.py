@@ -167,23 +167,29 @@ def test_config1_fp64_trajectory_and_gradients(oracle_mod):
 
 def test_config2_fp32_positions_and_gradients(oracle_mod):
     """32x32 sheet, top edge pinned, 60 steps of 1/60 s with seeded per-vertex forces,
-    FP32 path (CG tol 1e-6) vs the FP64 oracle (tol 1e-10): max position error
-    <= 1e-5 m, gradients w.r.t. Y, k_b, rho, forces and x0 within 1e-3 relative."""
+    FP32 path (CG tol 1e-6) vs the FP64 oracle (tol 1e-10) run on the same inputs (the
+    FP32 API receives x0, forces and material rounded to float; the oracle is given
+    those values): max position error <= 1e-5 m, gradients w.r.t. Y, k_b, rho, forces
+    and x0 within 1e-3 relative."""
     cfg = W.config2()
     s = cfg.sheets[0]
-    b, traj, status, refs = _rollout_both(oracle_mod, cfg.sheets, steps=cfg.steps, dt=cfg.dt, prec="f32",
-                                          tol=cfg.cg_tol, oracle_tol=1e-10, forces=[s.forces])
-    tx, tv, it, st = refs[0]
-    assert int(status[0]) == 0
-    err = np.abs(to_np(traj) - tx).max()
-    assert err <= 1e-5, err
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    x0, F, mat = f32(s.rest), f32(s.forces), f32(s.material)
+    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol)
+    traj, status = b.forward(to_cuda(mat[None], torch.float32), to_cuda(x0, torch.float32),
+                             torch.zeros(s.n, 3, dtype=torch.float32, device="cuda"), to_cuda(F, torch.float32))
     o = oracle_sims(oracle_mod, cfg.sheets)[0]
-    tgt = o.forward(s.material * np.array(cfg.target_scale), s.rest, np.zeros_like(s.rest), s.forces, dt=cfg.dt,
-                    steps=cfg.steps, tol=1e-10, max_iter=20000, gravity=W.GRAVITY)[0]
+    tx, tv, _, st = o.forward(mat, x0, np.zeros_like(x0), F, dt=cfg.dt, steps=cfg.steps, tol=1e-10, max_iter=20000,
+                              gravity=W.GRAVITY)
+    assert int(status[0]) == 0 and st == 0
+    err = np.abs(to_np(traj)[-1] - tx[-1]).max()
+    assert err <= 1e-5, err
+    tgt = o.forward(mat * np.array(cfg.target_scale), x0, np.zeros_like(x0), F, dt=cfg.dt, steps=cfg.steps,
+                    tol=1e-10, max_iter=20000, gravity=W.GRAVITY)[0]
     _, dL = oracle_mod.loss_l2(tx, tgt)
     _, dLg = b.loss_l2(traj, to_cuda(tgt, torch.float32))
     g = b.backward(dLg)
-    go = o.backward(s.material, tx, tv, dL, dt=cfg.dt, steps=cfg.steps, tol=1e-10, max_iter=20000, gravity=W.GRAVITY)
+    go = o.backward(mat, tx, tv, dL, dt=cfg.dt, steps=cfg.steps, tol=1e-10, max_iter=20000, gravity=W.GRAVITY)
     gm = to_np(g["material"])[0]
     for k in (0, 2, 3):
         assert gm[k] == pytest.approx(go["material"][k], rel=1e-3), k
