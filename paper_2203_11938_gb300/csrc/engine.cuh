@@ -804,17 +804,20 @@ __device__ __forceinline__ const R* adj_slot(const Dev<R>& d, int slot) {
 
 // RHS of the adjoint solve: mask(v_bar + h x_bar)
 template <class R>
-__global__ void k_adj_rhs(Dev<R> d, const R* __restrict__ ax, const R* __restrict__ av) {
+__global__ void k_adj_rhs(Dev<R> d, const double* __restrict__ ax, const double* __restrict__ av) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   V3<R> g = {R(0), R(0), R(0)};
-  if (!d.pinned[i]) g = axpy3(d.h, ld3(ax, i), ld3(av, i));
+  if (!d.pinned[i]) {
+    const V3<double> gd = axpy3((double)d.h, ld3(ax, i), ld3(av, i));
+    g = {(R)gd.x, (R)gd.y, (R)gd.z};
+  }
   st3(d.bvec, i, g);
 }
 
 // Per-vertex adjoint update after the element pass; lam = d.dv.
 template <class R>
-__global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, const double* __restrict__ v_t,
+__global__ void k_adj_vertex(Dev<R> d, double* __restrict__ ax, double* __restrict__ av, const double* __restrict__ v_t,
                              const double* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
@@ -829,11 +832,14 @@ __global__ void k_adj_vertex(Dev<R> d, R* __restrict__ ax, R* __restrict__ av, c
     r2.z += src[5];
   }
   const int u = d.i2u[i];
-  const V3<R> a_x = ld3(ax, i), a_v = ld3(av, i), lam = ld3r<R>(d.dv, i);
+  const V3<double> a_x = ld3(ax, i), a_v = ld3(av, i), lam = ld3(d.dv, i);
   const V3<R> dl = (dLdx_row && u >= 0) ? ld3(dLdx_row, u) : V3<R>{R(0), R(0), R(0)};
-  st3(ax, i, V3<R>{a_x.x + r1.x + dl.x, a_x.y + r1.y + dl.y, a_x.z + r1.z + dl.z});
-  st3(av, i, V3<R>{a_v.x + d.h * a_x.x + r2.x, a_v.y + d.h * a_x.y + r2.y, a_v.z + d.h * a_x.z + r2.z});
-  if (gF_row && u >= 0) st3(gF_row, u, V3<R>{d.h * lam.x, d.h * lam.y, d.h * lam.z});
+  const double h = (double)d.h;
+  st3(ax, i, V3<double>{a_x.x + (double)r1.x + (double)dl.x, a_x.y + (double)r1.y + (double)dl.y,
+                        a_x.z + (double)r1.z + (double)dl.z});
+  st3(av, i, V3<double>{a_v.x + h * a_x.x + (double)r2.x, a_v.y + h * a_x.y + (double)r2.y,
+                        a_v.z + h * a_x.z + (double)r2.z});
+  if (gF_row && u >= 0) st3(gF_row, u, V3<R>{(R)(h * lam.x), (R)(h * lam.y), (R)(h * lam.z)});
   const V3<double> vt = ld3(v_t, i), vt1 = ld3(v_t1, i);
   const double m1 = (double)d.area3[i];
   d.row_sc[i] = m1 * ((double)lam.x * ((double)d.h * (double)d.gx - (vt1.x - vt.x)) +

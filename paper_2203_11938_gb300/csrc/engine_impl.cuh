@@ -139,8 +139,8 @@ class Engine final : public EngineBase {
       ck_x_ = alloc<double>(n3 * nseg_, &rc);
       ck_v_ = alloc<double>(n3 * nseg_, &rc);
     }
-    ax_ = alloc<R>(n3, &rc);
-    av_ = alloc<R>(n3, &rc);
+    ax_ = alloc<double>(n3, &rc);  // adjoint accumulators x_bar, v_bar in FP64
+    av_ = alloc<double>(n3, &rc);
     tmp_a_ = alloc<R>(n3, &rc);
     tmp_b_ = alloc<R>(n3, &rc);
     tmp_xd_ = alloc<double>(n3, &rc);
@@ -565,8 +565,8 @@ class Engine final : public EngineBase {
     launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseBackward);
     launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseRecompute);
     CLOTH_CUDA(cudaMemsetAsync(d_.gacc, 0, sizeof(double) * 3 * L_.S, st));
-    gather((const R*)dL_dx + (size_t)T_ * nu3, ax_, st);
-    CLOTH_CUDA(cudaMemsetAsync(av_, 0, sizeof(R) * n3(), st));
+    gather_state((const R*)dL_dx + (size_t)T_ * nu3, ax_, st);
+    CLOTH_CUDA(cudaMemsetAsync(av_, 0, sizeof(double) * n3(), st));
     const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
     for (int k = nseg_ - 1; k >= 0; --k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
@@ -586,7 +586,7 @@ class Engine final : public EngineBase {
         // A_t at x_t (the RHS of the step matrix is not needed)
         elements(sx(j), nullptr, st);
         launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, (const R*)nullptr);
-        launch(k_adj_rhs<R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)ax_, (const R*)av_);
+        launch(k_adj_rhs<R>, dim3(grid_rows()), dim3(256), st, d_, (const double*)ax_, (const double*)av_);
         CLOTH_CUDA(cudaGetLastError());
         CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap));
         if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
@@ -599,8 +599,8 @@ class Engine final : public EngineBase {
       }
     }
     if (g_material) launch(k_grad_material<R>, dim3((L_.S + 127) / 128), dim3(128), st, d_, (R*)g_material);
-    if (g_x0) launch(k_scatter<R, R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)ax_, (R*)g_x0);
-    if (g_v0) launch(k_scatter<R, R>, dim3(grid_rows()), dim3(256), st, d_, (const R*)av_, (R*)g_v0);
+    if (g_x0) launch(k_scatter<R, double>, dim3(grid_rows()), dim3(256), st, d_, (const double*)ax_, (R*)g_x0);
+    if (g_v0) launch(k_scatter<R, double>, dim3(grid_rows()), dim3(256), st, d_, (const double*)av_, (R*)g_v0);
     launch(k_status_out<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, status);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
@@ -653,7 +653,8 @@ class Engine final : public EngineBase {
   bool have_forward_ = false;
   double *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;
   double *tmp_xd_ = nullptr, *tmp_vd_ = nullptr, *tmp_ud_ = nullptr;
-  R *ax_ = nullptr, *av_ = nullptr, *tmp_a_ = nullptr, *tmp_b_ = nullptr;
+  double *ax_ = nullptr, *av_ = nullptr;
+  R *tmp_a_ = nullptr, *tmp_b_ = nullptr;
   R *mat_ = nullptr, *mat_tmp_ = nullptr;
   double* lpart_ = nullptr;
   int* host_active_ = nullptr;
