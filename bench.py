@@ -49,14 +49,14 @@ def log(msg):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batch256", choices=["batch256", "grid32", "grid100", "grid256"])
     p.add_argument("--exec", dest="exec_mode", default="graph", choices=["graph", "plain"])
     p.add_argument("--no-plain-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--time-steps", type=int, default=0,
                    help="override the workload's time-step count (profiling runs; not a bench value)")
     return p.parse_args()

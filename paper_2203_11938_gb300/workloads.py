@@ -146,8 +146,10 @@ def config2(force_reading="area", force_sigma=0.05, steps=60):
     N = 32
     sigma = force_sigma * (1.0 / (N - 1)) ** 2 if force_reading == "area" else force_sigma
     F = gaussian_forces(N * N, steps, sigma, seed=0)
+    # CG tol 1e-8: at 1e-6 positions already meet 1e-5 m but dL/dx0 is limited to ~1.5e-3 by the
+    # solve tolerance (the FP64 path shows the same); 1e-8 brings every gradient under 1e-3.
     return Workload(f"grid32_fp32_{steps}steps", [_sheet(N, "top", BASE_MATERIAL, F)], 1.0 / 60.0, steps, "f32",
-                    1e-6)
+                    1e-8)
 
 
 def sample_material(rng):
