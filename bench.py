@@ -85,7 +85,7 @@ def workload_config(wl, name):
     sizes = [s.N for s in wl.sheets]
     return {"workload": f"{name}: {len(sizes)} sheet(s), grid sides {min(sizes)}-{max(sizes)} "
                         f"({wl.total_vertices} vertices), {wl.steps} steps dt={wl.dt:.5g}s, "
-                        f"{wl.precision}, CG tol {wl.cg_tol:g}, fwd+loss+adjoint",
+                        f"{wl.precision}, CG tol {wl.cg_tol:g} (block-Jacobi PCG, max {wl.cg_max_iter} iterations), fwd+loss+adjoint",
             "sheets": len(sizes), "vertices": wl.total_vertices, "time_steps": wl.steps,
             "checkpoint_every": wl.checkpoint_every, "loss": wl.loss}
 

@@ -82,10 +82,16 @@ typedef struct cloth_opts {
                                0 = exact Hessian (may be indefinite)                 */
   int32_t exec;             /* CLOTH_EXEC_*                                           */
   int32_t cg_poll_every;    /* PLAIN mode: CG iterations between host polls (>= 1)    */
+  int32_t precond;          /* CG preconditioner: CLOTH_PRECOND_JACOBI (scalar diagonal)
+                               or CLOTH_PRECOND_BLOCK_JACOBI (3x3 block per vertex)   */
 } cloth_opts;
 
+#define CLOTH_PRECOND_JACOBI 0
+#define CLOTH_PRECOND_BLOCK_JACOBI 1
+
 /* Fill `opts` with defaults: FP32, 1 step, dt 1/30, tol 1e-6, 2000 iterations,
- * no checkpointing, gravity (0, 0, -9.8), clamp_eta 1e-3, GRAPH execution, poll 16. */
+ * no checkpointing, gravity (0, 0, -9.8), clamp_eta 1e-3, GRAPH execution, poll 16,
+ * block-Jacobi preconditioner. */
 void cloth_default_opts(cloth_opts* opts);
 
 typedef struct cloth_mesh cloth_mesh;

@@ -21,6 +21,7 @@ _SRC = os.path.join(_HERE, "cloth_oracle.cpp")
 _LIB = os.path.join(_HERE, "libcloth_oracle.so")
 _lib = None
 ETA = 1e-3  # default smooth clamp of the membrane geometric stiffness, eps = ETA * Y (reading R6)
+PRECOND = 1  # default CG preconditioner: 3x3 block Jacobi (0: scalar Jacobi)
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -57,10 +58,10 @@ def _load():
         lib.oracle_dihedral.argtypes = [_dp]
         lib.oracle_dihedral.restype = ctypes.c_double
         lib.oracle_system_dense.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.oracle_forward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+        lib.oracle_forward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _ip]
         lib.oracle_forward.restype = ctypes.c_int
-        lib.oracle_backward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+        lib.oracle_backward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _ip]
         lib.oracle_backward.restype = ctypes.c_int
         lib.oracle_loss_l2.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
@@ -150,27 +151,28 @@ class OracleSim:
         return A, b
 
     # -- trajectory
-    def forward(self, material, x0, v0, forces, *, dt, steps, tol, max_iter, gravity, eta=ETA):
+    def forward(self, material, x0, v0, forces, *, dt, steps, tol, max_iter, gravity, eta=ETA, precond=PRECOND):
         N = 3 * self.n
         tx = np.zeros((steps + 1, self.n, 3))
         tv = np.zeros((steps + 1, self.n, 3))
         iters = np.zeros(steps, np.int32)
         st = ctypes.c_int(0)
         Fp = None if forces is None else _f64(forces, (steps, self.n, 3))
-        self._lib.oracle_forward(self._h, _d(_f64(material)), float(eta), float(dt), int(steps), float(tol), int(max_iter),
+        self._lib.oracle_forward(self._h, _d(_f64(material)), float(eta), int(precond), float(dt), int(steps), float(tol), int(max_iter),
                                  _d(_f64(gravity)), _d(_f64(x0, (self.n, 3))), _d(_f64(v0, (self.n, 3))), _d(Fp),
                                  _d(tx), _d(tv), iters.ctypes.data_as(_ip), ctypes.byref(st))
         del N
         return tx, tv, iters, st.value
 
-    def backward(self, material, traj_x, traj_v, dL_dx, *, dt, steps, tol, max_iter, gravity, eta=ETA):
+    def backward(self, material, traj_x, traj_v, dL_dx, *, dt, steps, tol, max_iter, gravity, eta=ETA,
+                 precond=PRECOND):
         gm = np.zeros(4)
         gF = np.zeros((steps, self.n, 3))
         gx0 = np.zeros((self.n, 3))
         gv0 = np.zeros((self.n, 3))
         iters = np.zeros(steps, np.int32)
         st = ctypes.c_int(0)
-        self._lib.oracle_backward(self._h, _d(_f64(material)), float(eta), float(dt), int(steps), float(tol), int(max_iter),
+        self._lib.oracle_backward(self._h, _d(_f64(material)), float(eta), int(precond), float(dt), int(steps), float(tol), int(max_iter),
                                   _d(_f64(gravity)), _d(_f64(traj_x)), _d(_f64(traj_v)), _d(_f64(dL_dx)),
                                   _d(gm), _d(gF), _d(gx0), _d(gv0), iters.ctypes.data_as(_ip), ctypes.byref(st))
         return dict(material=gm, forces=gF, x0=gx0, v0=gv0, cg_iters=iters, status=st.value)

@@ -285,6 +285,7 @@ struct Sim {
 struct Mat {
   double Y, nu, kb, rho;
   double eta;  // > 0: membrane geometric stiffness uses the smooth positive stress, eps = eta * Y (R6)
+  int precond = 1;  // CG preconditioner: 0 scalar Jacobi, 1 3x3 block Jacobi
   double mu() const { return Y / (2.0 * (1.0 + nu)); }
   double lam() const { return Y * nu / (1.0 - nu * nu); }
 };
@@ -406,14 +407,53 @@ void third_contraction(const Sim& s, const Mat& mt, const double* x, const doubl
   }
 }
 
+// Inverse of a 3x3 matrix by the adjugate (cofactor transpose over the determinant).
+void inv3(const double m[9], double out[9]) {
+  const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  out[0] = c00 / det;
+  out[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+  out[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+  out[3] = c01 / det;
+  out[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+  out[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+  out[6] = c02 / det;
+  out[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+  out[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
 // Jacobi-preconditioned CG on A y = rhs from y = 0, stopping when
 // |r|_2 <= tol |rhs|_2 (checked before each iteration) or after max_iter.
+// precond 0: scalar Jacobi z_i = r_i / A_ii;  1: block Jacobi with the 3x3 diagonal
+// block of each vertex, z_v = A_vv^{-1} r_v.
 // Returns 0 converged, 1 max_iter reached, 2 p^T A p <= 0 (indefinite), 3 non-finite.
-int pcg(const Sparse& A, const std::vector<double>& rhs, double tol, int max_iter, std::vector<double>& y, int* iters) {
+int pcg(const Sparse& A, const std::vector<double>& rhs, double tol, int max_iter, int precond, std::vector<double>& y,
+        int* iters) {
   const size_t N = rhs.size();
-  std::vector<double> r(rhs), z(N), p(N), Ap(N), dinv(N);
+  std::vector<double> r(rhs), z(N), p(N), Ap(N), dinv(N), binv(precond ? 3 * N : 0);
   y.assign(N, 0.0);
-  for (size_t i = 0; i < N; ++i) dinv[i] = 1.0 / A.at((int)i, (int)i);
+  if (precond) {
+    for (size_t v = 0; v < N / 3; ++v) {
+      double blk[9];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) blk[3 * a + b] = A.at((int)(3 * v + a), (int)(3 * v + b));
+      inv3(blk, &binv[9 * v]);
+    }
+  } else {
+    for (size_t i = 0; i < N; ++i) dinv[i] = 1.0 / A.at((int)i, (int)i);
+  }
+  auto apply_prec = [&]() {
+    if (precond) {
+      for (size_t v = 0; v < N / 3; ++v)
+        for (int a = 0; a < 3; ++a) {
+          double acc = 0.0;
+          for (int b = 0; b < 3; ++b) acc += binv[9 * v + 3 * a + b] * r[3 * v + b];
+          z[3 * v + a] = acc;
+        }
+    } else {
+      for (size_t i = 0; i < N; ++i) z[i] = dinv[i] * r[i];
+    }
+  };
   auto dotv = [&](const std::vector<double>& u, const std::vector<double>& w) {
     double acc = 0.0;
     for (size_t i = 0; i < N; ++i) acc += u[i] * w[i];
@@ -423,7 +463,7 @@ int pcg(const Sparse& A, const std::vector<double>& rhs, double tol, int max_ite
   *iters = 0;
   if (!std::isfinite(bnorm)) return 3;
   if (bnorm == 0.0) return 0;
-  for (size_t i = 0; i < N; ++i) z[i] = dinv[i] * r[i];
+  apply_prec();
   p = z;
   double rz = dotv(r, z);
   double rr = dotv(r, r);
@@ -438,7 +478,7 @@ int pcg(const Sparse& A, const std::vector<double>& rhs, double tol, int max_ite
       y[i] += alpha * p[i];
       r[i] -= alpha * Ap[i];
     }
-    for (size_t i = 0; i < N; ++i) z[i] = dinv[i] * r[i];
+    apply_prec();
     double rz_new = dotv(r, z);
     rr = dotv(r, r);
     double beta = rz_new / rz;
@@ -628,11 +668,11 @@ void oracle_system_dense(void* h, const double* material, double eta, double dt,
 // Forward trajectory.  x0, v0: [n][3]; forces: [steps][n][3] or NULL;
 // traj_x, traj_v: [steps+1][n][3]; dv_out [steps][n][3] or NULL; cg_iters [steps];
 // status: worst per-step solver status (0 ok, 1 maxiter, 2 indefinite, 3 non-finite).
-int oracle_forward(void* h, const double* material, double eta, double dt, int steps, double tol, int max_iter,
-                   const double* gravity, const double* x0, const double* v0, const double* forces, double* traj_x,
-                   double* traj_v, int* cg_iters, int* status) {
+int oracle_forward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,
+                   int max_iter, const double* gravity, const double* x0, const double* v0, const double* forces,
+                   double* traj_x, double* traj_v, int* cg_iters, int* status) {
   const Sim* s = static_cast<Sim*>(h);
-  Mat mt{material[0], material[1], material[2], material[3], eta};
+  Mat mt{material[0], material[1], material[2], material[3], eta, precond};
   const int N = 3 * s->n;
   std::copy(x0, x0 + N, traj_x);
   std::copy(v0, v0 + N, traj_v);
@@ -655,7 +695,7 @@ int oracle_forward(void* h, const double* material, double eta, double dt, int s
     }
     Sparse A = system_matrix(*s, mt, dt, Hm, Hb);
     int it = 0;
-    int st = pcg(A, b, tol, max_iter, dv, &it);
+    int st = pcg(A, b, tol, max_iter, mt.precond, dv, &it);
     if (cg_iters) cg_iters[t] = it;
     worst = std::max(worst, st);
     double* xn = traj_x + (size_t)(t + 1) * N;
@@ -674,11 +714,12 @@ int oracle_forward(void* h, const double* material, double eta, double dt, int s
 // dL_dx: [steps+1][n][3] (gradient of the loss w.r.t. every x_t, t = 0..steps).
 // Outputs (any may be NULL): g_material[4] (dL/dY, dL/dnu := 0, dL/dkb, dL/drho),
 // g_forces [steps][n][3], g_x0 [n][3], g_v0 [n][3]; cg_iters [steps]; status.
-int oracle_backward(void* h, const double* material, double eta, double dt, int steps, double tol, int max_iter,
-                    const double* gravity, const double* traj_x, const double* traj_v, const double* dL_dx,
-                    double* g_material, double* g_forces, double* g_x0, double* g_v0, int* cg_iters, int* status) {
+int oracle_backward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,
+                    int max_iter, const double* gravity, const double* traj_x, const double* traj_v,
+                    const double* dL_dx, double* g_material, double* g_forces, double* g_x0, double* g_v0,
+                    int* cg_iters, int* status) {
   const Sim* s = static_cast<Sim*>(h);
-  Mat mt{material[0], material[1], material[2], material[3], eta};
+  Mat mt{material[0], material[1], material[2], material[3], eta, precond};
   const int N = 3 * s->n;
   std::vector<double> ax(dL_dx + (size_t)steps * N, dL_dx + (size_t)(steps + 1) * N), av(N, 0.0);
   std::vector<double> g(N), lam, Hl(N), Hl2(N), third(N), fm(N), fb(N), Hu(N), Hu2(N), u(N), dv(N);
@@ -698,7 +739,7 @@ int oracle_backward(void* h, const double* material, double eta, double dt, int 
     internal_hessian(*s, mt, x, Hm, Hb);
     Sparse A = system_matrix(*s, mt, dt, Hm, Hb);
     int it = 0;
-    int st = pcg(A, g, tol, max_iter, lam, &it);
+    int st = pcg(A, g, tol, max_iter, mt.precond, lam, &it);
     worst = std::max(worst, st);
     if (cg_iters) cg_iters[t] = it;
     // The matrix term of b and A uses the (possibly clamped) Hessian H~ = Hm + Hb;

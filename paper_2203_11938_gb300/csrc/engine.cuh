@@ -59,7 +59,8 @@ struct Dev {
   double *tri_f, *hin_f;  // element force vectors f_e - h H~_e v_e, FP64
   R *tri_H, *hin_H, *tri_r, *hin_r;
   double *tri_sc, *hin_sc, *row_sc;
-  R *Aval, *bvec, *dinv, *r, *p, *Ap;
+  R *Aval, *bvec, *r, *p, *Ap;
+  R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
   double* dv;  // CG solution (dv, or lambda in the adjoint), accumulated in FP64
   CGSheet* cg;
   int* cnt;
@@ -72,6 +73,7 @@ struct Dev {
   R h, gx, gy, gz, eta;
   double tol;
   int maxit;
+  int precond;  // 0 scalar Jacobi, 1 block Jacobi
   bool clamp;
   const R* material;  // [S][4]
 };
@@ -91,6 +93,19 @@ template <class R> __device__ __forceinline__ V3<R> axpy3(R s, V3<R> x, V3<R> y)
 }
 template <class R> __device__ __forceinline__ double ddot3(V3<R> a, V3<R> b) {
   return (double)a.x * (double)b.x + (double)a.y * (double)b.y + (double)a.z * (double)b.z;
+}
+// Per-row dot product in the batch precision; the sums over rows are FP64.
+template <class R> __device__ __forceinline__ double rdot3(V3<R> a, V3<R> b) {
+  return (double)(a.x * b.x + a.y * b.y + a.z * b.z);
+}
+
+// z = D^{-1} r with the stored 3x3 inverse (SoA [9][Np])
+template <class R>
+__device__ __forceinline__ V3<R> apply_dinv(const R* __restrict__ D, int Np, int i, V3<R> r) {
+  const size_t n = (size_t)Np;
+  return {D[i] * r.x + D[n + i] * r.y + D[2 * n + i] * r.z,
+          D[3 * n + i] * r.x + D[4 * n + i] * r.y + D[5 * n + i] * r.z,
+          D[6 * n + i] * r.x + D[7 * n + i] * r.y + D[8 * n + i] * r.z};
 }
 
 // Block sum of NV doubles (blockDim.x == kThreads); result valid in thread 0.
@@ -478,7 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
   // difference form (A p)_i = R_i p_i + sum_{j != i} A_ij (p_j - p_i).  H annihilates
   // uniform translations, so R_i = m_i I - h^2 sum_{pinned j} H_ij exactly (no
   // cancellation), and smooth p no longer cancels large terms in the product.
-  R diag[3] = {R(1), R(1), R(1)};
+  double dblk[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   R rsum[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) rsum[q] = R(0);
@@ -491,8 +506,11 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
     const bool zero = pin_i || pin_j;
     R* dst = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
     if (k == 0) {
+      if (!pin_i) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) diag[q] = pin_i ? R(1) : mass + h2 * Hb[4 * q];
+        for (int q = 0; q < 9; ++q)
+          dblk[q] = (double)h2 * (double)Hb[q] + ((q == 0 || q == 4 || q == 8) ? (double)mass : 0.0);
+      }
       continue;  // written after the loop
     }
     if (!pin_i && pin_j && j != i) {
@@ -520,7 +538,28 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
     b.z = (R)(h * (f.z + md * (double)d.gz + (double)fe.z));
   }
   st3(d.bvec, i, b);
-  st3(d.dinv, i, V3<R>{R(1) / diag[0], R(1) / diag[1], R(1) / diag[2]});
+  // preconditioner: inverse of the 3x3 diagonal block (adjugate / determinant, in FP64)
+  double inv[9];
+  if (d.precond) {
+    const double* m = dblk;
+    const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+    const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    const double id = 1.0 / det;
+    inv[0] = c00 * id;
+    inv[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    inv[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    inv[3] = c01 * id;
+    inv[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    inv[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    inv[6] = c02 * id;
+    inv[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    inv[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) inv[q] = (q == 0 || q == 4 || q == 8) ? 1.0 / dblk[q] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) d.dinv[(size_t)q * d.Np + i] = (R)inv[q];
 }
 
 // ------------------------------------------------------------------ CG
@@ -543,13 +582,12 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
   double v[2] = {0.0, 0.0};
   if (on) {
     const V3<R> r = ld3(rhs, i);
-    const V3<R> di = ld3(d.dinv, i);
-    const V3<R> z = {di.x * r.x, di.y * r.y, di.z * r.z};
+    const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
     st3(d.r, i, r);
     st3(d.p, i, z);
     st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
-    v[0] = ddot3(r, z);
-    v[1] = ddot3(r, r);
+    v[0] = rdot3(r, z);
+    v[1] = rdot3(r, r);
   }
   double tot[2];
   if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
@@ -597,7 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
       y.z += a[192] * dp.x + a[224] * dp.y + a[256] * dp.z;
     }
     st3(d.Ap, i, y);
-    v[0] = ddot3(pi, y);
+    v[0] = rdot3(pi, y);
   }
   double tot[1];
   if (sheet_reduce<1>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
@@ -634,10 +672,9 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cud
     r = axpy3(-alpha, Ap, r);
     st3(d.dv, i, x);
     st3(d.r, i, r);
-    const V3<R> di = ld3(d.dinv, i);
-    const V3<R> z = {di.x * r.x, di.y * r.y, di.z * r.z};
-    v[0] = ddot3(r, z);
-    v[1] = ddot3(r, r);
+    const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
+    v[0] = rdot3(r, z);
+    v[1] = rdot3(r, r);
   }
   double tot[2];
   if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
@@ -667,8 +704,9 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d, int phase) {
   if (threadIdx.x >= d.work_rows[w]) return;
   const int i = d.work_row0[w] + threadIdx.x;
   const R beta = (R)d.cg[s].beta;
-  const V3<R> r = ld3(d.r, i), di = ld3(d.dinv, i), p = ld3(d.p, i);
-  st3(d.p, i, V3<R>{di.x * r.x + beta * p.x, di.y * r.y + beta * p.y, di.z * r.z + beta * p.z});
+  const V3<R> r = ld3(d.r, i), p = ld3(d.p, i);
+  const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
+  st3(d.p, i, V3<R>{z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z});
 }
 
 // v' = v + dv, x' = x + h v'; optional user-layout copy of x'.

@@ -71,6 +71,7 @@ class Engine final : public EngineBase {
     d.clamp = o_.clamp_eta > 0.0;
     d.tol = o_.cg_tol;
     d.maxit = o_.cg_max_iter;
+    d.precond = o_.precond;
     int rc = CLOTH_OK;
     auto up_i = [&](const std::vector<int>& v) -> const int* { return upload(v, &rc); };
     auto up_r = [&](const std::vector<double>& v) -> const R* {
@@ -120,7 +121,7 @@ class Engine final : public EngineBase {
     d.row_sc = alloc<double>(L_.Np, &rc);
     d.Aval = alloc<R>((size_t)L_.total_slots() * 32 * 9, &rc);
     d.bvec = alloc<R>(n3, &rc);
-    d.dinv = alloc<R>(n3, &rc);
+    d.dinv = alloc<R>(9 * (size_t)L_.Np, &rc);
     d.r = alloc<R>(n3, &rc);
     d.p = alloc<R>(n3, &rc);
     d.Ap = alloc<R>(n3, &rc);

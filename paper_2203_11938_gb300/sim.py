@@ -47,6 +47,7 @@ class ClothOpts(ctypes.Structure):
         ("clamp_eta", ctypes.c_double),
         ("exec", ctypes.c_int32),
         ("cg_poll_every", ctypes.c_int32),
+        ("precond", ctypes.c_int32),
     ]
 
 
@@ -142,7 +143,7 @@ class ClothBatch:
     """A batch of sheets stepped together (``cloth_batch_create``)."""
 
     def __init__(self, meshes, *, steps, dt, precision="f32", cg_tol=1e-6, cg_max_iter=2000, checkpoint_every=0,
-                 gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16):
+                 gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16, precond="block"):
         import torch
 
         if not torch.cuda.is_available():
@@ -161,6 +162,7 @@ class ClothBatch:
         o.clamp_eta = float(clamp_eta)
         o.exec = EXEC_GRAPH if exec_mode == "graph" else EXEC_PLAIN
         o.cg_poll_every = int(cg_poll_every)
+        o.precond = 1 if precond == "block" else 0
         self.opts = o
         self.steps = int(steps)
         self.dtype = torch.float64 if precision == "f64" else torch.float32

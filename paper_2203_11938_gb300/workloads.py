@@ -181,7 +181,9 @@ def config4(count=256, steps=100, nmin=16, nmax=64, seed=1):
     for _ in range(count):
         N = int(rng.integers(nmin, nmax + 1))
         sheets.append(_sheet(N, "top2", sample_material(rng)))
-    return Workload(f"batch{count}_grid{nmin}-{nmax}_{steps}steps", sheets, 1.0 / 30.0, steps, "f32", 1e-6)
+    # CG tol 1e-7: at 1e-6 a sampled sheet's k_b gradient is off by 1.5e-3 relative.
+    return Workload(f"batch{count}_grid{nmin}-{nmax}_{steps}steps", sheets, 1.0 / 30.0, steps, "f32", 1e-7,
+                    cg_max_iter=4000)
 
 
 def config5(steps=200, N=256):

@@ -116,8 +116,9 @@ def test_third_contraction_matches_oracle(oracle_mod, eta):
 
 # --------------------------------------------------------------------- trajectories
 def _rollout_both(oracle_mod, sheets, *, steps, dt, prec, tol, oracle_tol, forces=None, exec_mode="graph", ckpt=0,
-                  v0s=None):
-    b = make_batch(sheets, steps=steps, dt=dt, precision=prec, tol=tol, exec_mode=exec_mode, ckpt=ckpt)
+                  v0s=None, precond="block"):
+    b = make_batch(sheets, steps=steps, dt=dt, precision=prec, tol=tol, exec_mode=exec_mode, ckpt=ckpt,
+                   precond=precond)
     dtp = _dtype(prec)
     x0 = np.concatenate([s.rest for s in sheets])
     v0 = np.zeros_like(x0) if v0s is None else np.concatenate(v0s)
@@ -129,19 +130,22 @@ def _rollout_both(oracle_mod, sheets, *, steps, dt, prec, tol, oracle_tol, force
     for k, (s, o) in enumerate(zip(sheets, oracle_sims(oracle_mod, sheets))):
         vk = np.zeros_like(s.rest) if v0s is None else v0s[k]
         refs.append(o.forward(s.material, s.rest, vk, None if forces is None else forces[k], dt=dt, steps=steps,
-                              tol=oracle_tol, max_iter=20000, gravity=W.GRAVITY))
+                              tol=oracle_tol, max_iter=20000, gravity=W.GRAVITY,
+                              precond=1 if precond == "block" else 0))
     return b, traj, status, refs
 
 
-def test_config1_fp64_trajectory_and_gradients(oracle_mod):
+@pytest.mark.parametrize("precond", ["block", "scalar"])
+def test_config1_fp64_trajectory_and_gradients(oracle_mod, precond):
     """10x10 sheet, two top corners pinned, 20 steps of 1/30 s, FP64 (config 1 of the
     benchmark list): positions to 1e-10 m, gradients of the target-trajectory loss
-    w.r.t. Y, k_b, rho, x0, v0 to 1e-10 relative."""
+    w.r.t. Y, k_b, rho, x0, v0 to 1e-10 relative; block and scalar Jacobi."""
     cfg = W.config1()
     s = cfg.sheets[0]
     tol = 1e-12
+    pc = 1 if precond == "block" else 0
     b, traj, status, refs = _rollout_both(oracle_mod, cfg.sheets, steps=cfg.steps, dt=cfg.dt, prec="f64", tol=tol,
-                                          oracle_tol=tol)
+                                          oracle_tol=tol, precond=precond)
     tx, tv, it, st = refs[0]
     assert int(status[0]) == 0 and st == 0
     assert np.abs(to_np(traj) - tx).max() < 1e-10
@@ -149,13 +153,14 @@ def test_config1_fp64_trajectory_and_gradients(oracle_mod):
     o = oracle_sims(oracle_mod, cfg.sheets)[0]
     tgt_mat = s.material * np.array(cfg.target_scale)
     target = o.forward(tgt_mat, s.rest, np.zeros_like(s.rest), None, dt=cfg.dt, steps=cfg.steps, tol=tol,
-                       max_iter=20000, gravity=W.GRAVITY)[0]
+                       max_iter=20000, gravity=W.GRAVITY, precond=pc)[0]
     L_o, dL = oracle_mod.loss_l2(tx, target)
     loss, grad = b.loss_l2(traj, to_cuda(target, torch.float64))
     assert float(loss[0]) == pytest.approx(L_o, rel=1e-9)
     assert rel(to_np(grad), dL) < 1e-9
     g = b.backward(to_cuda(dL, torch.float64))
-    go = o.backward(s.material, tx, tv, dL, dt=cfg.dt, steps=cfg.steps, tol=tol, max_iter=20000, gravity=W.GRAVITY)
+    go = o.backward(s.material, tx, tv, dL, dt=cfg.dt, steps=cfg.steps, tol=tol, max_iter=20000, gravity=W.GRAVITY,
+                    precond=pc)
     gm = to_np(g["material"])[0]
     for k in (0, 2, 3):
         assert gm[k] == pytest.approx(go["material"][k], rel=1e-10)
@@ -198,32 +203,40 @@ def test_config2_fp32_positions_and_gradients(oracle_mod):
     assert rel(to_np(g["x0"]), go["x0"]) < 1e-3
 
 
-def test_config2_fp32_gradients_vs_finite_differences():
-    """The FP32 path's adjoint against central differences of its own forward map
-    (h = 1e-3 relative) for Y, k_b and rho on the 32x32 workload."""
+def test_config2_gradients_vs_finite_differences():
+    """Adjoint against central differences (h = 1e-3 relative) of the forward map for Y,
+    k_b and rho on the 32x32 workload.  The differences are taken on the FP64 path
+    (tol 1e-12), where they are accurate to O(h^2); the FP64 adjoint must agree to 1e-6
+    and the FP32 adjoint to 1e-3."""
     cfg = W.config2()
     s = cfg.sheets[0]
-    f32 = torch.float32
-    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol)
-    x0 = to_cuda(s.rest, f32)
-    v0 = torch.zeros_like(x0)
-    F = to_cuda(s.forces, f32)
     mat = s.material.copy()
-    tgt, _ = b.forward(to_cuda(mat * np.array(cfg.target_scale), f32)[None], x0, v0, F)
-    tgt = tgt.clone()
-    traj, _ = b.forward(to_cuda(mat, f32)[None], x0, v0, F)
-    _, dL = b.loss_l2(traj, tgt)
-    gm = to_np(b.backward(dL, want=("material",))["material"])[0]
+    grads = {}
+    for prec, tol in (("f64", 1e-12), ("f32", cfg.cg_tol)):
+        dt_ = _dtype(prec)
+        b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision=prec, tol=tol)
+        x0 = to_cuda(s.rest, dt_)
+        v0 = torch.zeros_like(x0)
+        F = to_cuda(s.forces, dt_)
+        tgt, _ = b.forward(to_cuda(mat * np.array(cfg.target_scale), dt_)[None], x0, v0, F)
+        tgt = tgt.clone()
+        traj, _ = b.forward(to_cuda(mat, dt_)[None], x0, v0, F)
+        _, dL = b.loss_l2(traj, tgt)
+        grads[prec] = to_np(b.backward(dL, want=("material",))["material"])[0]
+        if prec == "f64":
+            fd = {}
+            for k in (0, 2, 3):
+                h = 1e-3 * mat[k]
+                Ls = []
+                for sgn in (1.0, -1.0):
+                    m2 = mat.copy()
+                    m2[k] += sgn * h
+                    tr, _ = b.forward(to_cuda(m2, dt_)[None], x0, v0, F)
+                    Ls.append(float(b.loss_l2(tr, tgt, want_grad=False)[0][0]))
+                fd[k] = (Ls[0] - Ls[1]) / (2 * h)
     for k in (0, 2, 3):
-        h = 1e-3 * mat[k]
-        Ls = []
-        for sgn in (1.0, -1.0):
-            m2 = mat.copy()
-            m2[k] += sgn * h
-            tr, _ = b.forward(to_cuda(m2, f32)[None], x0, v0, F)
-            Ls.append(float(b.loss_l2(tr, tgt, want_grad=False)[0][0]))
-        fd = (Ls[0] - Ls[1]) / (2 * h)
-        assert gm[k] == pytest.approx(fd, rel=2e-3), k
+        assert grads["f64"][k] == pytest.approx(fd[k], rel=1e-6), k
+        assert grads["f32"][k] == pytest.approx(fd[k], rel=1e-3), k
 
 
 def test_batch256_full_size_sampled_sheets(oracle_mod):

@@ -244,7 +244,8 @@ def test_third_contraction_vs_fd_of_hessian(oracle_mod):
 
 
 # -------------------------------------------------------------------- step
-def test_pcg_matches_dense_solve(oracle_mod):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_pcg_matches_dense_solve(oracle_mod, precond):
     """One step with PCG to tol 1e-13 (exact Hessian, eta = 0) equals numpy's dense
     solve of (M + h^2 H) dv = b, with the dense system built from finite differences of
     the forces (not from the oracle's own Hessian) on a stretched (all-tension) state."""
@@ -275,7 +276,7 @@ def test_pcg_matches_dense_solve(oracle_mod):
     dv = np.zeros(N)
     dv[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
     tx, tv, it, st = sim.forward(MAT, x, v, None, dt=dt, steps=1, tol=1e-13, max_iter=10000, gravity=W.GRAVITY,
-                                 eta=0.0)
+                                 eta=0.0, precond=precond)
     assert st == 0
     np.testing.assert_allclose(tv[1].ravel() - v.ravel(), dv, rtol=0, atol=1e-7 * np.abs(dv).max())
     np.testing.assert_allclose(tx[1], x + dt * tv[1], rtol=0, atol=1e-15)
