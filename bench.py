@@ -319,19 +319,22 @@ def run_ours(args):
     torch.cuda.synchronize()
     mi = b.matrix_info()
     es = 4 if dtype == torch.float32 else 8
-    alg_bytes = mi["blocks"] * (9 * es + 4) + mi["rows"] * (2 * 3 * es)
+    # SpMV with the direction update folded in: per block 9 values + 1 column index; per row
+    # z_k and p_{k-1} read once, p_k and Ap written once (gathers of neighbours hit L1/L2)
+    alg_bytes = mi["blocks"] * (9 * es + 4) + mi["rows"] * (4 * 3 * es)
     spmv_ms = b.time_kernel("spmv", reps=50)
     upd_ms = b.time_kernel("cg_update", reps=50)
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (spmv_ms / 1e3) / 1e9
     traffic = committed_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (3x3-block SELL-32 SpMV + per-sheet FP64 p.Ap)",
+    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (p = z + beta p_old fused, 3x3-block SELL-32 SpMV, per-sheet FP64 p.Ap)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(spmv_ms, 5),
                 "bytes_per_vertex": round(alg_bytes / mi["rows"], 1),
                 "cg_update_ms": round(upd_ms, 5),
-                "cg_update_GBps": round(mi["rows"] * 3 * es * 7 / (upd_ms / 1e3) / 1e9, 1)}
+                # update: p, Ap, r, z (3 es each), dv FP64 read+write, r write, 3x3 inverse (9 es)
+                "cg_update_GBps": round(mi["rows"] * (3 * es * 5 + 9 * es + 48) / (upd_ms / 1e3) / 1e9, 1)}
 
     log(f"roofline {roofline}")
     # -------------------- plain single-sheet GPU path on a subset of the sheets

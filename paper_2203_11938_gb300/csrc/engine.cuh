@@ -59,7 +59,8 @@ struct Dev {
   double *tri_f, *hin_f;  // element force vectors f_e - h H~_e v_e, FP64
   R *tri_H, *hin_H, *tri_r, *hin_r;
   double *tri_sc, *hin_sc, *row_sc;
-  R *Aval, *bvec, *r, *p, *Ap;
+  R *Aval, *bvec, *r, *z, *Ap;
+  R* p;  // two direction buffers [2][Np][3] (p_k and p_{k-1})
   R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
   double* dv;  // CG solution (dv, or lambda in the adjoint), accumulated in FP64
   CGSheet* cg;
@@ -573,140 +574,174 @@ __global__ void k_cond_set(Dev<R> d, cudaGraphConditionalHandle cond) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, *d.active > 0 ? 1u : 0u);
 }
 
-// r = rhs, dv = 0, p = z = D^{-1} r; rz, rr, bb per sheet.
+// CG with the direction update folded into the SpMV (two kernels per iteration).
+// Iteration k of a sheet uses p_k = z_k + beta_k p_{k-1} (beta_0 = 0): the SpMV kernel
+// forms p_k for its own row (written to pbuf[k & 1]) and, on the fly, for every
+// gathered neighbour from z and pbuf[(k + 1) & 1] (= p_{k-1}) with the same fused
+// multiply-add, so the values are bitwise those a separate direction pass would write.
+// The update kernel stores z_{k+1} = D^{-1} r_{k+1}.  All CTAs loop over the work
+// entries (grid sized to the resident CTAs), skipping converged sheets.
+template <class R>
+__device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
+  return {fma(beta, pold.x, z.x), fma(beta, pold.y, z.y), fma(beta, pold.z, z.z)};
+}
+
+// r = rhs, dv = 0, z = D^{-1} r, p_{-1} = 0, beta_0 = 0; rz, rr, bb per sheet.
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restrict__ rhs, int phase) {
-  const int w = blockIdx.x, s = d.work_sheet[w];
-  const bool on = threadIdx.x < d.work_rows[w];
-  const int i = d.work_row0[w] + threadIdx.x;
-  double v[2] = {0.0, 0.0};
-  if (on) {
-    const V3<R> r = ld3(rhs, i);
-    const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
-    st3(d.r, i, r);
-    st3(d.p, i, z);
-    st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
-    v[0] = rdot3(r, z);
-    v[1] = rdot3(r, r);
-  }
-  double tot[2];
-  if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
-    CGSheet& c = d.cg[s];
-    c.rz = tot[0];
-    c.rr = tot[1];
-    c.bb = tot[1];
-    c.iters = 0;
-    c.done = 0;
-    bool fin = false;
-    if (!isfinite(tot[1])) {
-      c.status |= CLOTH_STATUS_NONFINITE;
-      fin = true;
-    } else if (tot[1] == 0.0 || sqrt(tot[1]) <= d.tol * sqrt(tot[1])) {
-      fin = true;
+  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
+    const int s = d.work_sheet[w];
+    const bool on = threadIdx.x < d.work_rows[w];
+    const int i = d.work_row0[w] + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (on) {
+      const V3<R> r = ld3(rhs, i);
+      const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
+      st3(d.r, i, r);
+      st3(d.z, i, z);
+      st3(d.p + 3 * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
+      st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
+      v[0] = rdot3(r, z);
+      v[1] = rdot3(r, r);
     }
-    if (fin) finish_sheet(d, s, phase, 0, 0);
+    double tot[2];
+    if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
+      CGSheet& c = d.cg[s];
+      c.rz = tot[0];
+      c.rr = tot[1];
+      c.bb = tot[1];
+      c.beta = 0.0;
+      c.iters = 0;
+      c.done = 0;
+      bool fin = false;
+      if (!isfinite(tot[1])) {
+        c.status |= CLOTH_STATUS_NONFINITE;
+        fin = true;
+      } else if (tot[1] == 0.0 || sqrt(tot[1]) <= d.tol * sqrt(tot[1])) {
+        fin = true;
+      }
+      if (fin) finish_sheet(d, s, phase, 0, 0);
+    }
   }
 }
 
-// Ap = A p (SELL-32 3x3 blocks), pAp per sheet, alpha = rz / pAp.
+// p_k = z_k + beta_k p_{k-1};  Ap = A p_k (SELL-32 3x3 blocks, difference form);
+// pAp per sheet, alpha = rz / pAp.
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
                                                       int use_cond) {
-  const int w = blockIdx.x, s = d.work_sheet[w];
-  if (d.cg[s].done) return;
-  const bool on = threadIdx.x < d.work_rows[w];
-  const int i = d.work_row0[w] + threadIdx.x;
-  double v[1] = {0.0};
-  if (on) {
-    const int sl = i >> 5, lane = i & 31;
-    const int K = d.slice_K[sl], base = d.slice_base[sl];
-    const V3<R> pi = ld3(d.p, i);
-    const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
-    V3<R> y = {a0[0] * pi.x + a0[32] * pi.y + a0[64] * pi.z, a0[96] * pi.x + a0[128] * pi.y + a0[160] * pi.z,
-               a0[192] * pi.x + a0[224] * pi.y + a0[256] * pi.z};
-    for (int k = 1; k < K; ++k) {
-      const int ent = (base + k) * 32 + lane;
-      const int j = d.cols[ent];
-      const R* a = d.Aval + (size_t)(base + k) * 32 * 9 + lane;
-      const V3<R> pj = ld3(d.p, j);
-      const V3<R> dp = {pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
-      y.x += a[0] * dp.x + a[32] * dp.y + a[64] * dp.z;
-      y.y += a[96] * dp.x + a[128] * dp.y + a[160] * dp.z;
-      y.z += a[192] * dp.x + a[224] * dp.y + a[256] * dp.z;
+  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
+    const int s = d.work_sheet[w];
+    if (d.cg[s].done) continue;  // uniform over the CTA
+    const int k = d.cg[s].iters;
+    const R beta = (R)d.cg[s].beta;
+    const R* __restrict__ pold = d.p + 3 * (size_t)d.Np * ((k + 1) & 1);
+    R* __restrict__ pnew = d.p + 3 * (size_t)d.Np * (k & 1);
+    const bool on = threadIdx.x < d.work_rows[w];
+    const int i = d.work_row0[w] + threadIdx.x;
+    double v[1] = {0.0};
+    if (on) {
+      const int sl = i >> 5, lane = i & 31;
+      const int K = d.slice_K[sl], base = d.slice_base[sl];
+      const V3<R> pi = next_dir(ld3(d.z, i), beta, ld3(pold, i));
+      st3(pnew, i, pi);
+      const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
+      V3<R> y = {a0[0] * pi.x + a0[32] * pi.y + a0[64] * pi.z, a0[96] * pi.x + a0[128] * pi.y + a0[160] * pi.z,
+                 a0[192] * pi.x + a0[224] * pi.y + a0[256] * pi.z};
+      int q = 1;
+      for (; q + 1 < K; q += 2) {  // two slots per iteration: more loads in flight
+        const int e0 = (base + q) * 32 + lane, e1 = e0 + 32;
+        const int j0 = d.cols[e0], j1 = d.cols[e1];
+        const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
+        const R* b = a + 32 * 9;
+        const V3<R> p0 = next_dir(ld3(d.z, j0), beta, ld3(pold, j0));
+        const V3<R> p1 = next_dir(ld3(d.z, j1), beta, ld3(pold, j1));
+        const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
+        const V3<R> d1 = {p1.x - pi.x, p1.y - pi.y, p1.z - pi.z};
+        y.x += a[0] * d0.x + a[32] * d0.y + a[64] * d0.z;
+        y.y += a[96] * d0.x + a[128] * d0.y + a[160] * d0.z;
+        y.z += a[192] * d0.x + a[224] * d0.y + a[256] * d0.z;
+        y.x += b[0] * d1.x + b[32] * d1.y + b[64] * d1.z;
+        y.y += b[96] * d1.x + b[128] * d1.y + b[160] * d1.z;
+        y.z += b[192] * d1.x + b[224] * d1.y + b[256] * d1.z;
+      }
+      if (q < K) {
+        const int e0 = (base + q) * 32 + lane;
+        const int j0 = d.cols[e0];
+        const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
+        const V3<R> p0 = next_dir(ld3(d.z, j0), beta, ld3(pold, j0));
+        const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
+        y.x += a[0] * d0.x + a[32] * d0.y + a[64] * d0.z;
+        y.y += a[96] * d0.x + a[128] * d0.y + a[160] * d0.z;
+        y.z += a[192] * d0.x + a[224] * d0.y + a[256] * d0.z;
+      }
+      st3(d.Ap, i, y);
+      v[0] = rdot3(pi, y);
     }
-    st3(d.Ap, i, y);
-    v[0] = rdot3(pi, y);
-  }
-  double tot[1];
-  if (sheet_reduce<1>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
-    CGSheet& c = d.cg[s];
-    c.pAp = tot[0];
-    if (!isfinite(tot[0])) {
-      c.status |= CLOTH_STATUS_NONFINITE;
-      finish_sheet(d, s, phase, cond, use_cond);
-    } else if (tot[0] <= 0.0) {
-      c.status |= CLOTH_STATUS_INDEFINITE;
-      finish_sheet(d, s, phase, cond, use_cond);
-    } else {
-      c.alpha = c.rz / tot[0];
+    double tot[1];
+    if (sheet_reduce<1>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
+      CGSheet& c = d.cg[s];
+      c.pAp = tot[0];
+      if (!isfinite(tot[0])) {
+        c.status |= CLOTH_STATUS_NONFINITE;
+        finish_sheet(d, s, phase, cond, use_cond);
+      } else if (tot[0] <= 0.0) {
+        c.status |= CLOTH_STATUS_INDEFINITE;
+        finish_sheet(d, s, phase, cond, use_cond);
+      } else {
+        c.alpha = c.rz / tot[0];
+      }
     }
   }
 }
 
-// dv += alpha p, r -= alpha Ap, z = D^{-1} r; rz, rr; beta; convergence.
+// dv += alpha p_k (FP64), r -= alpha Ap, z = D^{-1} r (stored); rz, rr; beta; convergence.
+// Also counts the loop-body executions of this phase.
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
                                                         int use_cond) {
-  const int w = blockIdx.x, s = d.work_sheet[w];
-  if (d.cg[s].done) return;
-  const bool on = threadIdx.x < d.work_rows[w];
-  const int i = d.work_row0[w] + threadIdx.x;
-  const R alpha = (R)d.cg[s].alpha;
-  double v[2] = {0.0, 0.0};
-  if (on) {
-    const V3<R> p = ld3(d.p, i), Ap = ld3(d.Ap, i);
-    V3<double> x = ld3(d.dv, i);
-    V3<R> r = ld3(d.r, i);
-    const double al = d.cg[s].alpha;
-    x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
-    r = axpy3(-alpha, Ap, r);
-    st3(d.dv, i, x);
-    st3(d.r, i, r);
-    const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
-    v[0] = rdot3(r, z);
-    v[1] = rdot3(r, r);
-  }
-  double tot[2];
-  if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
-    CGSheet& c = d.cg[s];
-    c.beta = tot[0] / c.rz;
-    c.rz = tot[0];
-    c.rr = tot[1];
-    c.iters += 1;
-    if (!isfinite(tot[1]) || !isfinite(tot[0])) {
-      c.status |= CLOTH_STATUS_NONFINITE;
-      finish_sheet(d, s, phase, cond, use_cond);
-    } else if (sqrt(tot[1]) <= d.tol * sqrt(c.bb)) {
-      finish_sheet(d, s, phase, cond, use_cond);
-    } else if (c.iters >= d.maxit) {
-      c.status |= CLOTH_STATUS_CG_MAXITER;
-      finish_sheet(d, s, phase, cond, use_cond);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.body_runs[phase] += 1ull;
+  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
+    const int s = d.work_sheet[w];
+    if (d.cg[s].done) continue;
+    const int k = d.cg[s].iters;
+    const R* __restrict__ pk = d.p + 3 * (size_t)d.Np * (k & 1);
+    const bool on = threadIdx.x < d.work_rows[w];
+    const int i = d.work_row0[w] + threadIdx.x;
+    const R alpha = (R)d.cg[s].alpha;
+    double v[2] = {0.0, 0.0};
+    if (on) {
+      const V3<R> p = ld3(pk, i), Ap = ld3(d.Ap, i);
+      V3<double> x = ld3(d.dv, i);
+      V3<R> r = ld3(d.r, i);
+      const double al = d.cg[s].alpha;
+      x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
+      r = axpy3(-alpha, Ap, r);
+      st3(d.dv, i, x);
+      st3(d.r, i, r);
+      const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
+      st3(d.z, i, z);
+      v[0] = rdot3(r, z);
+      v[1] = rdot3(r, r);
+    }
+    double tot[2];
+    if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
+      CGSheet& c = d.cg[s];
+      c.beta = tot[0] / c.rz;
+      c.rz = tot[0];
+      c.rr = tot[1];
+      c.iters += 1;
+      if (!isfinite(tot[1]) || !isfinite(tot[0])) {
+        c.status |= CLOTH_STATUS_NONFINITE;
+        finish_sheet(d, s, phase, cond, use_cond);
+      } else if (sqrt(tot[1]) <= d.tol * sqrt(c.bb)) {
+        finish_sheet(d, s, phase, cond, use_cond);
+      } else if (c.iters >= d.maxit) {
+        c.status |= CLOTH_STATUS_CG_MAXITER;
+        finish_sheet(d, s, phase, cond, use_cond);
+      }
     }
   }
-}
-
-// p = D^{-1} r + beta p  (also counts the loop-body executions of this phase)
-template <class R>
-__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d, int phase) {
-  const int w = blockIdx.x, s = d.work_sheet[w];
-  if (w == 0 && threadIdx.x == 0) d.body_runs[phase] += 1ull;
-  if (d.cg[s].done) return;
-  if (threadIdx.x >= d.work_rows[w]) return;
-  const int i = d.work_row0[w] + threadIdx.x;
-  const R beta = (R)d.cg[s].beta;
-  const V3<R> r = ld3(d.r, i), p = ld3(d.p, i);
-  const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
-  st3(d.p, i, V3<R>{z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z});
 }
 
 // v' = v + dv, x' = x + h v'; optional user-layout copy of x'.

@@ -123,7 +123,8 @@ class Engine final : public EngineBase {
     d.bvec = alloc<R>(n3, &rc);
     d.dinv = alloc<R>(9 * (size_t)L_.Np, &rc);
     d.r = alloc<R>(n3, &rc);
-    d.p = alloc<R>(n3, &rc);
+    d.p = alloc<R>(2 * n3, &rc);
+    d.z = alloc<R>(n3, &rc);
     d.Ap = alloc<R>(n3, &rc);
     d.dv = alloc<double>(n3, &rc);
     d.cg = alloc<CGSheet>(L_.S, &rc);
@@ -166,6 +167,16 @@ class Engine final : public EngineBase {
       *err = "CUDA setup failed";
       return CLOTH_ERR_CUDA;
     }
+    // CG kernels: as many CTAs as can be resident at once, each looping over work entries
+    int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R>, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_update<R>, kThreads, 0) != cudaSuccess) {
+      *err = "CUDA occupancy query failed";
+      return CLOTH_ERR_CUDA;
+    }
+    cg_grid_ = std::max(1, std::min(d.NW, sms * std::max(1, std::min(per_sm, per_sm2))));
     return CLOTH_OK;
   }
 
@@ -237,7 +248,7 @@ class Engine final : public EngineBase {
     if (fwd) *fwd = (int64_t)h[0];
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
-    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + 3 * (int64_t)(b[0] + b[1] + b[2]);
+    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + 2 * (int64_t)(b[0] + b[1] + b[2]);
     return CLOTH_OK;
   }
 
@@ -265,8 +276,8 @@ class Engine final : public EngineBase {
     const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
     auto one = [&]() {
       switch (which) {
-        case 0: k_cg_spmv<R><<<d_.NW, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
-        case 1: k_cg_update<R><<<d_.NW, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
+        case 0: k_cg_spmv<R><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
+        case 1: k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
         case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr); break;
         case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
         default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
@@ -468,7 +479,7 @@ class Engine final : public EngineBase {
   // conditional WHILE node whose condition the kernels clear when the last sheet ends.
   int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
     launch(k_solve_begin<R>, dim3(1), dim3(32), st, d_);
-    launch(k_cg_init<R>, dim3(d_.NW), dim3(kThreads), st, d_, rhs, phase);
+    launch(k_cg_init<R>, dim3(cg_grid_), dim3(kThreads), st, d_, rhs, phase);
     CLOTH_CUDA(cudaGetLastError());
     if (capturing) {
       cudaStreamCaptureStatus cs;
@@ -490,9 +501,8 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
       cudaGraph_t body = cp.conditional.phGraph_out[0];
       CLOTH_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      k_cg_spmv<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
-      k_cg_update<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
-      k_cg_dir<R><<<d_.NW, kThreads, 0, body_stream_>>>(d_, phase);
+      k_cg_spmv<R><<<cg_grid_, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
+      k_cg_update<R><<<cg_grid_, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
       cudaGraph_t out = nullptr;
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
@@ -505,9 +515,8 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamSynchronize(st));
       if (*host_active_ <= 0 || launched >= o_.cg_max_iter) break;
       for (int k = 0; k < poll; ++k) {
-        k_cg_spmv<R><<<d_.NW, kThreads, 0, st>>>(d_, phase, 0, 0);
-        k_cg_update<R><<<d_.NW, kThreads, 0, st>>>(d_, phase, 0, 0);
-        k_cg_dir<R><<<d_.NW, kThreads, 0, st>>>(d_, phase);
+        k_cg_spmv<R><<<cg_grid_, kThreads, 0, st>>>(d_, phase, 0, 0);
+        k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_, phase, 0, 0);
       }
       launched += poll;
       CLOTH_CUDA(cudaGetLastError());
@@ -662,6 +671,7 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;
   std::vector<CachedGraph> graphs_;
   int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
+  int cg_grid_ = 1;  // CTAs of the CG kernels
   cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
   std::vector<void*> allocs_;
   size_t bytes_ = 0;
