@@ -319,15 +319,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     mi = b.matrix_info()
     es = 4 if dtype == torch.float32 else 8
-    # SpMV with the direction update folded in: per block 9 values + 1 column index; per row
-    # z_k and p_{k-1} read once, p_k and Ap written once (gathers of neighbours hit L1/L2)
-    alg_bytes = mi["blocks"] * (9 * es + 4) + mi["rows"] * (4 * 3 * es)
+    # per block 9 values + 1 column index; per row: fused schedule (bit 1) reads z_k and
+    # p_{k-1} and writes p_k and Ap, else reads p_k and writes Ap (neighbour gathers hit L1/L2)
+    fused = bool(mi["cg_schedule"] & 2)
+    alg_bytes = mi["blocks"] * (9 * es + 4) + mi["rows"] * ((4 if fused else 2) * 3 * es)
     spmv_ms = b.time_kernel("spmv", reps=50)
     upd_ms = b.time_kernel("cg_update", reps=50)
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (spmv_ms / 1e3) / 1e9
     traffic = committed_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (p = z + beta p_old fused, 3x3-block SELL-32 SpMV, per-sheet FP64 p.Ap)",
+    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (3x3-block SELL-32 difference-form SpMV, per-sheet FP64 p.Ap)",
+                "cg_schedule": mi["cg_schedule"],
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(spmv_ms, 5),

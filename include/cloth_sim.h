@@ -84,6 +84,12 @@ typedef struct cloth_opts {
   int32_t cg_poll_every;    /* PLAIN mode: CG iterations between host polls (>= 1)    */
   int32_t precond;          /* CG preconditioner: CLOTH_PRECOND_JACOBI (scalar diagonal)
                                or CLOTH_PRECOND_BLOCK_JACOBI (3x3 block per vertex)   */
+  int32_t cg_schedule;      /* CG kernel schedule, all with bitwise-identical results:
+                               -1 = autotune at cloth_batch_create (times each schedule
+                               on the batch's matrix, caches the choice in the JSON file
+                               $CLOTH_TUNE_CACHE or ~/.cache/cloth_sim/tune.json);
+                               0..3: bit 1 = direction update folded into the SpMV,
+                               bit 0 = resident-CTA grid looping over rows             */
 } cloth_opts;
 
 #define CLOTH_PRECOND_JACOBI 0
@@ -91,7 +97,7 @@ typedef struct cloth_opts {
 
 /* Fill `opts` with defaults: FP32, 1 step, dt 1/30, tol 1e-6, 2000 iterations,
  * no checkpointing, gravity (0, 0, -9.8), clamp_eta 1e-3, GRAPH execution, poll 16,
- * block-Jacobi preconditioner. */
+ * block-Jacobi preconditioner, autotuned CG schedule. */
 void cloth_default_opts(cloth_opts* opts);
 
 typedef struct cloth_mesh cloth_mesh;
@@ -163,9 +169,10 @@ int cloth_stats(cloth_batch* batch, int64_t* fwd_cg_iters, int64_t* bwd_cg_iters
 
 /* Size of the step matrix A (Eq. 4-5) in 3x3 blocks: rows (vertices, each sheet
  * padded to a multiple of 32), blocks (structurally nonzero blocks) and
- * stored_blocks (blocks stored by the SELL-32 layout, padding included). */
+ * stored_blocks (blocks stored by the SELL-32 layout, padding included); cg_schedule:
+ * the CG kernel schedule in use (0..3, see cloth_opts).  Any pointer may be NULL. */
 int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks,
-                      int64_t* stored_blocks);
+                      int64_t* stored_blocks, int32_t* cg_schedule);
 
 /* Average device time [ms] of `reps` back-to-back launches of one step kernel on
  * the state left by the last call, timed with CUDA events on `stream`:

@@ -53,6 +53,7 @@ void cloth_default_opts(cloth_opts* o) {
   o->exec = CLOTH_EXEC_GRAPH;
   o->cg_poll_every = 16;
   o->precond = CLOTH_PRECOND_BLOCK_JACOBI;
+  o->cg_schedule = -1;
 }
 
 int cloth_mesh_create(const double* rest_xyz, int32_t n, const int32_t* tris, int32_t m, const uint8_t* pinned,
@@ -90,7 +91,8 @@ int cloth_batch_create(const cloth_mesh* const* meshes, int32_t count, const clo
     return fail(CLOTH_ERR_INVALID_ARG, "cloth_batch_create: precision must be CLOTH_FP32 or CLOTH_FP64");
   if (o.steps < 1 || !(o.dt > 0.0) || !(o.cg_tol >= 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 ||
       !(o.clamp_eta >= 0.0) || (o.exec != CLOTH_EXEC_PLAIN && o.exec != CLOTH_EXEC_GRAPH) || o.cg_poll_every < 1 ||
-      (o.precond != CLOTH_PRECOND_JACOBI && o.precond != CLOTH_PRECOND_BLOCK_JACOBI))
+      (o.precond != CLOTH_PRECOND_JACOBI && o.precond != CLOTH_PRECOND_BLOCK_JACOBI) || o.cg_schedule < -1 ||
+      o.cg_schedule > 3)
     return fail(CLOTH_ERR_INVALID_ARG, "cloth_batch_create: invalid option value");
   std::vector<const cloth::MeshData*> sheets;
   for (int i = 0; i < count; ++i) {
@@ -156,9 +158,10 @@ int cloth_stats(cloth_batch* batch, int64_t* fwd, int64_t* bwd, int64_t* rec, in
   return batch->engine->stats(fwd, bwd, rec, launches);
 }
 
-int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks, int64_t* stored_blocks) {
+int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks, int64_t* stored_blocks,
+                      int32_t* cg_schedule) {
   CLOTH_NEED_BATCH("cloth_matrix_info");
-  return batch->engine->matrix_info(rows, blocks, stored_blocks);
+  return batch->engine->matrix_info(rows, blocks, stored_blocks, cg_schedule);
 }
 
 int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* avg_ms, void* stream) {

@@ -586,7 +586,7 @@ __device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
   return {fma(beta, pold.x, z.x), fma(beta, pold.y, z.y), fma(beta, pold.z, z.z)};
 }
 
-// r = rhs, dv = 0, z = D^{-1} r, p_{-1} = 0, beta_0 = 0; rz, rr, bb per sheet.
+// r = rhs, dv = 0, z = D^{-1} r, p_0 = z, p_{-1} = 0, beta_0 = 0; rz, rr, bb per sheet.
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restrict__ rhs, int phase) {
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
@@ -599,7 +599,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
       st3(d.r, i, r);
       st3(d.z, i, z);
-      st3(d.p + 3 * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
+      st3(d.p, i, z);                                             // p_0 (buffer 0), unfused schedule
+      st3(d.p + 3 * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1), fused schedule
       st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
       v[0] = rdot3(r, z);
       v[1] = rdot3(r, r);
@@ -625,9 +626,10 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
   }
 }
 
-// p_k = z_k + beta_k p_{k-1};  Ap = A p_k (SELL-32 3x3 blocks, difference form);
-// pAp per sheet, alpha = rz / pAp.
-template <class R>
+// Ap = A p_k (SELL-32 3x3 blocks, difference form); pAp per sheet, alpha = rz / pAp.
+// FUSED: p_k = z_k + beta_k p_{k-1} is formed here (own row written, neighbours on the
+// fly); otherwise p_k was written by k_cg_dir.
+template <class R, bool FUSED>
 __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
                                                       int use_cond) {
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
@@ -643,8 +645,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
     if (on) {
       const int sl = i >> 5, lane = i & 31;
       const int K = d.slice_K[sl], base = d.slice_base[sl];
-      const V3<R> pi = next_dir(ld3(d.z, i), beta, ld3(pold, i));
-      st3(pnew, i, pi);
+      V3<R> pi;
+      if (FUSED) {
+        pi = next_dir(ld3(d.z, i), beta, ld3(pold, i));
+        st3(pnew, i, pi);
+      } else {
+        pi = ld3(pnew, i);
+      }
       const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
       V3<R> y = {a0[0] * pi.x + a0[32] * pi.y + a0[64] * pi.z, a0[96] * pi.x + a0[128] * pi.y + a0[160] * pi.z,
                  a0[192] * pi.x + a0[224] * pi.y + a0[256] * pi.z};
@@ -654,8 +661,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
         const int j0 = d.cols[e0], j1 = d.cols[e1];
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
         const R* b = a + 32 * 9;
-        const V3<R> p0 = next_dir(ld3(d.z, j0), beta, ld3(pold, j0));
-        const V3<R> p1 = next_dir(ld3(d.z, j1), beta, ld3(pold, j1));
+        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ld3(pold, j0)) : ld3(pnew, j0);
+        const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ld3(pold, j1)) : ld3(pnew, j1);
         const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
         const V3<R> d1 = {p1.x - pi.x, p1.y - pi.y, p1.z - pi.z};
         y.x += a[0] * d0.x + a[32] * d0.y + a[64] * d0.z;
@@ -669,7 +676,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
         const int e0 = (base + q) * 32 + lane;
         const int j0 = d.cols[e0];
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
-        const V3<R> p0 = next_dir(ld3(d.z, j0), beta, ld3(pold, j0));
+        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ld3(pold, j0)) : ld3(pnew, j0);
         const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
         y.x += a[0] * d0.x + a[32] * d0.y + a[64] * d0.z;
         y.y += a[96] * d0.x + a[128] * d0.y + a[160] * d0.z;
@@ -692,6 +699,22 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
         c.alpha = c.rz / tot[0];
       }
     }
+  }
+}
+
+// p_{k+1} = z_{k+1} + beta_{k+1} p_k (unfused schedule), after the update of iteration k
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
+  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
+    const int s = d.work_sheet[w];
+    if (d.cg[s].done) continue;
+    if (threadIdx.x >= d.work_rows[w]) continue;
+    const int k = d.cg[s].iters;  // already k + 1 after the update
+    const R beta = (R)d.cg[s].beta;
+    const R* __restrict__ pold = d.p + 3 * (size_t)d.Np * ((k + 1) & 1);
+    R* __restrict__ pnew = d.p + 3 * (size_t)d.Np * (k & 1);
+    const int i = d.work_row0[w] + threadIdx.x;
+    st3(pnew, i, next_dir(ld3(d.z, i), beta, ld3(pold, i)));
   }
 }
 

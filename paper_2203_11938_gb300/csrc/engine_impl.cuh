@@ -2,7 +2,12 @@
 #pragma once
 
 #include <cstdio>
+#include <cstdlib>
+#include <filesystem>
+#include <fstream>
+#include <map>
 #include <memory>
+#include <sstream>
 #include <string>
 #include <utility>
 #include <vector>
@@ -171,12 +176,19 @@ class Engine final : public EngineBase {
     int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R>, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R, true>, kThreads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_update<R>, kThreads, 0) != cudaSuccess) {
       *err = "CUDA occupancy query failed";
       return CLOTH_ERR_CUDA;
     }
     cg_grid_ = std::max(1, std::min(d.NW, sms * std::max(1, std::min(per_sm, per_sm2))));
+    resident_grid_ = cg_grid_;
+    if (o_.cg_schedule >= 0) {
+      set_schedule(o_.cg_schedule);
+    } else {
+      int rc2 = autotune(err);
+      if (rc2 != CLOTH_OK) return rc2;
+    }
     return CLOTH_OK;
   }
 
@@ -248,11 +260,12 @@ class Engine final : public EngineBase {
     if (fwd) *fwd = (int64_t)h[0];
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
-    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + 2 * (int64_t)(b[0] + b[1] + b[2]);
+    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + (sched_fused_ ? 2 : 3) * (int64_t)(b[0] + b[1] + b[2]);
     return CLOTH_OK;
   }
 
-  int matrix_info(int64_t* rows, int64_t* blocks, int64_t* slots) override {
+  int matrix_info(int64_t* rows, int64_t* blocks, int64_t* slots, int32_t* schedule) override {
+    if (schedule) *schedule = schedule_;
     if (rows) *rows = L_.Np;
     if (blocks) {
       int64_t nb = 0;
@@ -276,7 +289,10 @@ class Engine final : public EngineBase {
     const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
     auto one = [&]() {
       switch (which) {
-        case 0: k_cg_spmv<R><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
+        case 0:
+          if (sched_fused_) k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0);
+          else k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0);
+          break;
         case 1: k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
         case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr); break;
         case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
@@ -475,6 +491,133 @@ class Engine final : public EngineBase {
     return CLOTH_OK;
   }
 
+  // CG schedules (bitwise-identical results): bit 1 = direction update folded into the
+  // SpMV (2 kernels per iteration) else a separate direction kernel (3); bit 0 = grid of
+  // resident CTAs looping over work entries else one CTA per work entry.
+  void set_schedule(int sched) {
+    schedule_ = sched & 3;
+    sched_fused_ = (schedule_ & 2) != 0;
+    cg_grid_ = (schedule_ & 1) ? resident_grid_ : d_.NW;
+  }
+
+  void emit_cg_body(cudaStream_t s, int phase, cudaGraphConditionalHandle cond, int use_cond) {
+    if (sched_fused_) {
+      k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
+      k_cg_update<R><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
+    } else {
+      k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
+      k_cg_update<R><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
+      k_cg_dir<R><<<cg_grid_, kThreads, 0, s>>>(d_);
+    }
+  }
+
+  static std::string tune_cache_path() {
+    if (const char* p = std::getenv("CLOTH_TUNE_CACHE")) return p;
+    const char* base = std::getenv("XDG_CACHE_HOME");
+    std::string dir = base ? std::string(base) : (std::getenv("HOME") ? std::string(std::getenv("HOME")) + "/.cache" : "");
+    if (dir.empty()) return "";
+    return dir + "/cloth_sim/tune.json";
+  }
+
+  // Flat JSON object {"key": value, ...} of integer schedule choices.
+  static std::map<std::string, int> read_tune_cache(const std::string& path) {
+    std::map<std::string, int> m;
+    std::ifstream f(path);
+    if (!f) return m;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string t = ss.str();
+    size_t i = 0;
+    while ((i = t.find('"', i)) != std::string::npos) {
+      const size_t j = t.find('"', i + 1);
+      if (j == std::string::npos) break;
+      const size_t c = t.find(':', j);
+      if (c == std::string::npos) break;
+      m[t.substr(i + 1, j - i - 1)] = std::atoi(t.c_str() + c + 1);
+      i = t.find_first_of(",}", c);
+      if (i == std::string::npos) break;
+    }
+    return m;
+  }
+
+  static void write_tune_cache(const std::string& path, const std::map<std::string, int>& m) {
+    std::error_code ec;
+    std::filesystem::create_directories(std::filesystem::path(path).parent_path(), ec);
+    std::ofstream f(path, std::ios::trunc);
+    if (!f) return;
+    f << "{";
+    bool first = true;
+    for (const auto& kv : m) {
+      f << (first ? "" : ",") << "\n  \"" << kv.first << "\": " << kv.second;
+      first = false;
+    }
+    f << "\n}\n";
+  }
+
+  // Autotuner: time one CG iteration of every schedule on this batch's matrix (assembled
+  // at the rest state with a nominal material) and keep the fastest; the choice is cached
+  // per device and matrix shape in a JSON file.
+  int autotune(std::string* err) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+      *err = "device query failed";
+      return CLOTH_ERR_CUDA;
+    }
+    std::ostringstream key;
+    key << prop.name << "|" << (sizeof(R) == 4 ? "f32" : "f64") << "|rows=" << L_.Np << "|entries=" << d_.NW
+        << "|slots=" << L_.total_slots();
+    const std::string path = tune_cache_path();
+    auto cache = path.empty() ? std::map<std::string, int>() : read_tune_cache(path);
+    auto it = cache.find(key.str());
+    if (it != cache.end()) {
+      set_schedule(it->second);
+      return CLOTH_OK;
+    }
+    cudaStream_t st = cap_stream_;
+    std::vector<R> mat(4 * (size_t)L_.S);
+    for (int s = 0; s < L_.S; ++s) {
+      mat[4 * s] = R(1e3);
+      mat[4 * s + 1] = R(0.3);
+      mat[4 * s + 2] = R(1e-4);
+      mat[4 * s + 3] = R(0.1);
+    }
+    CLOTH_CUDA(cudaMemcpy(mat_tmp_, mat.data(), sizeof(R) * mat.size(), cudaMemcpyHostToDevice));
+    CLOTH_CUDA(cudaMemcpy(tmp_xd_, L_.rest.data(), sizeof(double) * L_.rest.size(), cudaMemcpyHostToDevice));
+    CLOTH_CUDA(cudaMemset(tmp_vd_, 0, sizeof(double) * n3()));
+    d_.material = mat_tmp_;
+    elements(tmp_xd_, tmp_vd_, st);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr);
+    float best = 1e30f;
+    int best_s = 3;
+    const int iters = 12;
+    for (int sched = 0; sched < 4; ++sched) {
+      set_schedule(sched);
+      k_solve_begin<R><<<1, 32, 0, st>>>(d_);
+      k_cg_init<R><<<cg_grid_, kThreads, 0, st>>>(d_, d_.bvec, kPhaseForward);
+      emit_cg_body(st, kPhaseForward, 0, 0);  // warm-up
+      CLOTH_CUDA(cudaEventRecord(ev0_, st));
+      for (int k = 0; k < iters; ++k) emit_cg_body(st, kPhaseForward, 0, 0);
+      CLOTH_CUDA(cudaEventRecord(ev1_, st));
+      CLOTH_CUDA(cudaEventSynchronize(ev1_));
+      float ms = 0.f;
+      CLOTH_CUDA(cudaEventElapsedTime(&ms, ev0_, ev1_));
+      if (ms < best) {
+        best = ms;
+        best_s = sched;
+      }
+    }
+    set_schedule(best_s);
+    d_.material = mat_;
+    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
+    CLOTH_CUDA(cudaStreamSynchronize(st));
+    if (!path.empty()) {
+      cache[key.str()] = best_s;
+      write_tune_cache(path, cache);
+    }
+    return CLOTH_OK;
+  }
+
   // Solve A y = rhs (y left in d_.dv) for every sheet.  In graph mode the CG loop is a
   // conditional WHILE node whose condition the kernels clear when the last sheet ends.
   int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
@@ -501,8 +644,7 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
       cudaGraph_t body = cp.conditional.phGraph_out[0];
       CLOTH_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      k_cg_spmv<R><<<cg_grid_, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
-      k_cg_update<R><<<cg_grid_, kThreads, 0, body_stream_>>>(d_, phase, cond, 1);
+      emit_cg_body(body_stream_, phase, cond, 1);
       cudaGraph_t out = nullptr;
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
@@ -515,8 +657,7 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamSynchronize(st));
       if (*host_active_ <= 0 || launched >= o_.cg_max_iter) break;
       for (int k = 0; k < poll; ++k) {
-        k_cg_spmv<R><<<cg_grid_, kThreads, 0, st>>>(d_, phase, 0, 0);
-        k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_, phase, 0, 0);
+        emit_cg_body(st, phase, 0, 0);
       }
       launched += poll;
       CLOTH_CUDA(cudaGetLastError());
@@ -671,7 +812,10 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;
   std::vector<CachedGraph> graphs_;
   int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
-  int cg_grid_ = 1;  // CTAs of the CG kernels
+  int cg_grid_ = 1;       // CTAs of the CG kernels (the schedule's choice)
+  int resident_grid_ = 1; // CTAs resident at once on the whole GPU
+  bool sched_fused_ = true;
+  int schedule_ = 3;
   cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
   std::vector<void*> allocs_;
   size_t bytes_ = 0;

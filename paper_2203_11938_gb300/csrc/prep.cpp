@@ -193,6 +193,7 @@ void build_layout(const std::vector<const MeshData*>& sheets, BatchLayout* Lp) {
   L.i2u.assign(L.Np, -1);
   L.u2i.assign(L.Nu, -1);
   L.pinned.assign(L.Np, 1);
+  L.rest.assign(3 * (size_t)L.Np, 0.0);
   L.area3.assign(L.Np, 0.0);
   L.vsheet.assign(L.Np, 0);
   L.usheet.assign(L.Nu, 0);
@@ -242,6 +243,7 @@ void build_layout(const std::vector<const MeshData*>& sheets, BatchLayout* Lp) {
       L.u2i[uoff + u] = i;
       L.pinned[i] = d.pinned[u];
       L.area3[i] = d.area3[u];
+      for (int c = 0; c < 3; ++c) L.rest[3 * (size_t)i + c] = d.rest[3 * (size_t)u + c];
       L.usheet[uoff + u] = s;
       std::vector<int>& rc = rowcols[i];
       rc.push_back(i);

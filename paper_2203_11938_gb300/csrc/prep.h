@@ -44,6 +44,7 @@ struct BatchLayout {
   std::vector<int> i2u;            // [Np] internal -> user index, -1 for padding
   std::vector<int> u2i;            // [Nu]
   std::vector<uint8_t> pinned;     // [Np] padding rows count as pinned
+  std::vector<double> rest;        // [Np][3] rest positions (0 for padding rows)
   std::vector<double> area3;       // [Np]
   std::vector<int> vsheet;         // [Np]
   std::vector<int> usheet;         // [Nu] sheet of each user vertex

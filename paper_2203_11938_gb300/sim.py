@@ -48,6 +48,7 @@ class ClothOpts(ctypes.Structure):
         ("exec", ctypes.c_int32),
         ("cg_poll_every", ctypes.c_int32),
         ("precond", ctypes.c_int32),
+        ("cg_schedule", ctypes.c_int32),
     ]
 
 
@@ -80,7 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_loss_l2.argtypes = [_vp] * 6
     lib.cloth_loss_pinhole.argtypes = [_vp] * 7
     lib.cloth_stats.argtypes = [_vp] * 5
-    lib.cloth_matrix_info.argtypes = [_vp] * 4
+    lib.cloth_matrix_info.argtypes = [_vp] * 5
     lib.cloth_time_kernel.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.cloth_internal_forces.argtypes = [_vp] * 6
     lib.cloth_system_dense.argtypes = [_vp] * 8
@@ -143,7 +144,8 @@ class ClothBatch:
     """A batch of sheets stepped together (``cloth_batch_create``)."""
 
     def __init__(self, meshes, *, steps, dt, precision="f32", cg_tol=1e-6, cg_max_iter=2000, checkpoint_every=0,
-                 gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16, precond="block"):
+                 gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16, precond="block",
+                 cg_schedule=-1):
         import torch
 
         if not torch.cuda.is_available():
@@ -163,6 +165,7 @@ class ClothBatch:
         o.exec = EXEC_GRAPH if exec_mode == "graph" else EXEC_PLAIN
         o.cg_poll_every = int(cg_poll_every)
         o.precond = 1 if precond == "block" else 0
+        o.cg_schedule = int(cg_schedule)
         self.opts = o
         self.steps = int(steps)
         self.dtype = torch.float64 if precision == "f64" else torch.float32
@@ -273,10 +276,10 @@ class ClothBatch:
                 "kernel_launches": n.value}
 
     def matrix_info(self):
-        r, b, s = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(_lib.cloth_matrix_info(self._h, ctypes.byref(r), ctypes.byref(b), ctypes.byref(s)),
+        r, b, s, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.cloth_matrix_info(self._h, ctypes.byref(r), ctypes.byref(b), ctypes.byref(s), ctypes.byref(c)),
                "cloth_matrix_info")
-        return {"rows": r.value, "blocks": b.value, "stored_blocks": s.value}
+        return {"rows": r.value, "blocks": b.value, "stored_blocks": s.value, "cg_schedule": c.value}
 
     KERNELS = {"spmv": 0, "cg_update": 1, "assemble": 2, "elem_tri": 3, "elem_hinge": 4}
 
