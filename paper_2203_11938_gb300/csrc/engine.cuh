@@ -89,6 +89,22 @@ template <class R> __device__ __forceinline__ void st3(R* a, int i, V3<R> v) {
   a[3 * (size_t)i + 2] = v.z;
 }
 template <class R> __device__ __forceinline__ V3<R> add3(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+
+// CG direction vectors are the gathered operand of the SpMV: in FP32 they are stored as
+// 16-byte float4 (x, y, z, 0) so a neighbour gather is one aligned load.
+template <class R> struct PStride { static constexpr int v = 3; };
+template <> struct PStride<float> { static constexpr int v = 4; };
+template <class R> __device__ __forceinline__ V3<R> ldp(const R* a, int i) { return ld3(a, i); }
+template <> __device__ __forceinline__ V3<float> ldp<float>(const float* a, int i) {
+  const float4 q = reinterpret_cast<const float4*>(a)[i];
+  return {q.x, q.y, q.z};
+}
+template <class R> __device__ __forceinline__ void stp(R* a, int i, V3<R> v) { st3(a, i, v); }
+template <> __device__ __forceinline__ void stp<float>(float* a, int i, V3<float> v) {
+  reinterpret_cast<float4*>(a)[i] = make_float4(v.x, v.y, v.z, 0.f);
+}
+// streamed (read-once) matrix data: do not keep in L1
+template <class R> __device__ __forceinline__ R lds(const R* a) { return __ldcs(a); }
 template <class R> __device__ __forceinline__ V3<R> axpy3(R s, V3<R> x, V3<R> y) {
   return {s * x.x + y.x, s * x.y + y.y, s * x.z + y.z};
 }
@@ -599,8 +615,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
       st3(d.r, i, r);
       st3(d.z, i, z);
-      st3(d.p, i, z);                                             // p_0 (buffer 0), unfused schedule
-      st3(d.p + 3 * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1), fused schedule
+      stp(d.p, i, z);                                                          // p_0 (buffer 0), unfused
+      stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1), fused
       st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
       v[0] = rdot3(r, z);
       v[1] = rdot3(r, r);
@@ -637,8 +653,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
     if (d.cg[s].done) continue;  // uniform over the CTA
     const int k = d.cg[s].iters;
     const R beta = (R)d.cg[s].beta;
-    const R* __restrict__ pold = d.p + 3 * (size_t)d.Np * ((k + 1) & 1);
-    R* __restrict__ pnew = d.p + 3 * (size_t)d.Np * (k & 1);
+    const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
+    R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const bool on = threadIdx.x < d.work_rows[w];
     const int i = d.work_row0[w] + threadIdx.x;
     double v[1] = {0.0};
@@ -647,40 +663,47 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
       const int K = d.slice_K[sl], base = d.slice_base[sl];
       V3<R> pi;
       if (FUSED) {
-        pi = next_dir(ld3(d.z, i), beta, ld3(pold, i));
-        st3(pnew, i, pi);
+        pi = next_dir(ld3(d.z, i), beta, ldp(pold, i));
+        stp(pnew, i, pi);
       } else {
-        pi = ld3(pnew, i);
+        pi = ldp(pnew, i);
       }
       const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
-      V3<R> y = {a0[0] * pi.x + a0[32] * pi.y + a0[64] * pi.z, a0[96] * pi.x + a0[128] * pi.y + a0[160] * pi.z,
-                 a0[192] * pi.x + a0[224] * pi.y + a0[256] * pi.z};
+      V3<R> y = {lds(a0) * pi.x + lds(a0 + 32) * pi.y + lds(a0 + 64) * pi.z,
+                 lds(a0 + 96) * pi.x + lds(a0 + 128) * pi.y + lds(a0 + 160) * pi.z,
+                 lds(a0 + 192) * pi.x + lds(a0 + 224) * pi.y + lds(a0 + 256) * pi.z};
       int q = 1;
       for (; q + 1 < K; q += 2) {  // two slots per iteration: more loads in flight
         const int e0 = (base + q) * 32 + lane, e1 = e0 + 32;
-        const int j0 = d.cols[e0], j1 = d.cols[e1];
+        const int j0 = lds(d.cols + e0), j1 = lds(d.cols + e1);
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
         const R* b = a + 32 * 9;
-        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ld3(pold, j0)) : ld3(pnew, j0);
-        const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ld3(pold, j1)) : ld3(pnew, j1);
+        R av[9], bv[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          av[t] = lds(a + 32 * t);
+          bv[t] = lds(b + 32 * t);
+        }
+        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
+        const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ldp(pold, j1)) : ldp(pnew, j1);
         const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
         const V3<R> d1 = {p1.x - pi.x, p1.y - pi.y, p1.z - pi.z};
-        y.x += a[0] * d0.x + a[32] * d0.y + a[64] * d0.z;
-        y.y += a[96] * d0.x + a[128] * d0.y + a[160] * d0.z;
-        y.z += a[192] * d0.x + a[224] * d0.y + a[256] * d0.z;
-        y.x += b[0] * d1.x + b[32] * d1.y + b[64] * d1.z;
-        y.y += b[96] * d1.x + b[128] * d1.y + b[160] * d1.z;
-        y.z += b[192] * d1.x + b[224] * d1.y + b[256] * d1.z;
+        y.x += av[0] * d0.x + av[1] * d0.y + av[2] * d0.z;
+        y.y += av[3] * d0.x + av[4] * d0.y + av[5] * d0.z;
+        y.z += av[6] * d0.x + av[7] * d0.y + av[8] * d0.z;
+        y.x += bv[0] * d1.x + bv[1] * d1.y + bv[2] * d1.z;
+        y.y += bv[3] * d1.x + bv[4] * d1.y + bv[5] * d1.z;
+        y.z += bv[6] * d1.x + bv[7] * d1.y + bv[8] * d1.z;
       }
       if (q < K) {
         const int e0 = (base + q) * 32 + lane;
-        const int j0 = d.cols[e0];
+        const int j0 = lds(d.cols + e0);
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
-        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ld3(pold, j0)) : ld3(pnew, j0);
+        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
         const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
-        y.x += a[0] * d0.x + a[32] * d0.y + a[64] * d0.z;
-        y.y += a[96] * d0.x + a[128] * d0.y + a[160] * d0.z;
-        y.z += a[192] * d0.x + a[224] * d0.y + a[256] * d0.z;
+        y.x += lds(a) * d0.x + lds(a + 32) * d0.y + lds(a + 64) * d0.z;
+        y.y += lds(a + 96) * d0.x + lds(a + 128) * d0.y + lds(a + 160) * d0.z;
+        y.z += lds(a + 192) * d0.x + lds(a + 224) * d0.y + lds(a + 256) * d0.z;
       }
       st3(d.Ap, i, y);
       v[0] = rdot3(pi, y);
@@ -711,10 +734,10 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
     if (threadIdx.x >= d.work_rows[w]) continue;
     const int k = d.cg[s].iters;  // already k + 1 after the update
     const R beta = (R)d.cg[s].beta;
-    const R* __restrict__ pold = d.p + 3 * (size_t)d.Np * ((k + 1) & 1);
-    R* __restrict__ pnew = d.p + 3 * (size_t)d.Np * (k & 1);
+    const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
+    R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const int i = d.work_row0[w] + threadIdx.x;
-    st3(pnew, i, next_dir(ld3(d.z, i), beta, ld3(pold, i)));
+    stp(pnew, i, next_dir(ld3(d.z, i), beta, ldp(pold, i)));
   }
 }
 
@@ -728,13 +751,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cud
     const int s = d.work_sheet[w];
     if (d.cg[s].done) continue;
     const int k = d.cg[s].iters;
-    const R* __restrict__ pk = d.p + 3 * (size_t)d.Np * (k & 1);
+    const R* __restrict__ pk = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const bool on = threadIdx.x < d.work_rows[w];
     const int i = d.work_row0[w] + threadIdx.x;
     const R alpha = (R)d.cg[s].alpha;
     double v[2] = {0.0, 0.0};
     if (on) {
-      const V3<R> p = ld3(pk, i), Ap = ld3(d.Ap, i);
+      const V3<R> p = ldp(pk, i), Ap = ld3(d.Ap, i);
       V3<double> x = ld3(d.dv, i);
       V3<R> r = ld3(d.r, i);
       const double al = d.cg[s].alpha;

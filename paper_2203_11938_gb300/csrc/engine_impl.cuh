@@ -128,7 +128,7 @@ class Engine final : public EngineBase {
     d.bvec = alloc<R>(n3, &rc);
     d.dinv = alloc<R>(9 * (size_t)L_.Np, &rc);
     d.r = alloc<R>(n3, &rc);
-    d.p = alloc<R>(2 * n3, &rc);
+    d.p = alloc<R>(2 * (size_t)PStride<R>::v * L_.Np, &rc);
     d.z = alloc<R>(n3, &rc);
     d.Ap = alloc<R>(n3, &rc);
     d.dv = alloc<double>(n3, &rc);
