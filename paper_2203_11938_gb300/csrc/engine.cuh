@@ -64,8 +64,7 @@ struct Dev {
   R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
   double* dv;  // CG solution (dv, or lambda in the adjoint), accumulated in FP64
   CGSheet* cg;
-  int* cnt;
-  double* part;
+  double *part_a, *part_b;  // per-warp partial sums [NW * 8]
   int* active;
   unsigned long long* iter_total;
   unsigned long long* body_runs;  // [3] CG loop-body executions per phase
@@ -148,41 +147,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
   }
   __syncthreads();
-}
-
-// Segmented reduction over the work entries of sheet s.  Every CTA of the sheet calls
-// this once; the last CTA to arrive sums all partials in entry order (deterministic)
-// and returns true with the totals in thread 0's `tot`.  No CTA waits for another.
-template <int NV>
-__device__ bool sheet_reduce(double (&v)[NV], int w, int s, const int* wfirst, double* part, int* cnt,
-                             double (&tot)[NV]) {
-  __shared__ int is_last;
-  block_sum<NV>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[(size_t)w * NV + k] = v[k];
-    __threadfence();
-    const int nb = wfirst[s + 1] - wfirst[s];
-    is_last = (atomicAdd(&cnt[s], 1) == nb - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  const int w0 = wfirst[s], nb = wfirst[s + 1] - w0;
-  double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int e = threadIdx.x; e < nb; e += kThreads) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&part[(size_t)(w0 + e) * NV + k]);
-  }
-  block_sum<NV>(acc);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
-    cnt[s] = 0;
-  }
-  return true;
 }
 
 template <class R>
@@ -590,64 +554,94 @@ __global__ void k_cond_set(Dev<R> d, cudaGraphConditionalHandle cond) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, *d.active > 0 ? 1u : 0u);
 }
 
-// CG with the direction update folded into the SpMV (two kernels per iteration).
-// Iteration k of a sheet uses p_k = z_k + beta_k p_{k-1} (beta_0 = 0): the SpMV kernel
-// forms p_k for its own row (written to pbuf[k & 1]) and, on the fly, for every
-// gathered neighbour from z and pbuf[(k + 1) & 1] (= p_{k-1}) with the same fused
-// multiply-add, so the values are bitwise those a separate direction pass would write.
-// The update kernel stores z_{k+1} = D^{-1} r_{k+1}.  All CTAs loop over the work
-// entries (grid sized to the resident CTAs), skipping converged sheets.
+// Jacobi-PCG over all sheets at once.  The streaming kernels (init, SpMV, update,
+// direction) write one FP64 partial sum per warp and use no barrier, fence or atomic;
+// a per-sheet scalar kernel (one warp per sheet, fixed summation order, hence
+// deterministic) then forms alpha, or beta and the convergence test.  Iteration k of a
+// sheet uses p_k = z_k + beta_k p_{k-1} (beta_0 = 0), kept in pbuf[k & 1]; the SpMV either
+// forms p_k itself (FUSED: own row written, neighbours on the fly, same fused multiply-add,
+// so bitwise the values k_cg_dir would write) or reads what k_cg_dir wrote.
 template <class R>
 __device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
   return {fma(beta, pold.x, z.x), fma(beta, pold.y, z.y), fma(beta, pold.z, z.z)};
 }
 
-// r = rhs, dv = 0, z = D^{-1} r, p_0 = z, p_{-1} = 0, beta_0 = 0; rz, rr, bb per sheet.
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// partial of warp `wp` (0..7) of work entry w: index w * 8 + wp
+constexpr int kWarpsPerEntry = kThreads / 32;
+
+// r = rhs, dv = 0, z = D^{-1} r, p_0 = z, p_{-1} = 0; partials of r.z and r.r.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restrict__ rhs, int phase) {
+__global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restrict__ rhs) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
-    const int s = d.work_sheet[w];
     const bool on = threadIdx.x < d.work_rows[w];
     const int i = d.work_row0[w] + threadIdx.x;
-    double v[2] = {0.0, 0.0};
+    double v0 = 0.0, v1 = 0.0;
     if (on) {
       const V3<R> r = ld3(rhs, i);
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
       st3(d.r, i, r);
       st3(d.z, i, z);
-      stp(d.p, i, z);                                                          // p_0 (buffer 0), unfused
-      stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1), fused
+      stp(d.p, i, z);                                                          // p_0 (buffer 0)
+      stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
       st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
-      v[0] = rdot3(r, z);
-      v[1] = rdot3(r, r);
+      v0 = rdot3(r, z);
+      v1 = rdot3(r, r);
     }
-    double tot[2];
-    if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
-      CGSheet& c = d.cg[s];
-      c.rz = tot[0];
-      c.rr = tot[1];
-      c.bb = tot[1];
-      c.beta = 0.0;
-      c.iters = 0;
-      c.done = 0;
-      bool fin = false;
-      if (!isfinite(tot[1])) {
-        c.status |= CLOTH_STATUS_NONFINITE;
-        fin = true;
-      } else if (tot[1] == 0.0 || sqrt(tot[1]) <= d.tol * sqrt(tot[1])) {
-        fin = true;
-      }
-      if (fin) finish_sheet(d, s, phase, 0, 0);
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+      d.part_a[(size_t)w * kWarpsPerEntry + wp] = v0;
+      d.part_b[(size_t)w * kWarpsPerEntry + wp] = v1;
     }
   }
 }
 
-// Ap = A p_k (SELL-32 3x3 blocks, difference form); pAp per sheet, alpha = rz / pAp.
-// FUSED: p_k = z_k + beta_k p_{k-1} is formed here (own row written, neighbours on the
-// fly); otherwise p_k was written by k_cg_dir.
+// Sum over the warp partials of sheet s (one warp, lane-strided then shuffle tree).
+template <class R>
+__device__ __forceinline__ double sheet_sum(const Dev<R>& d, const double* part, int s) {
+  const int lane = threadIdx.x & 31;
+  const int p0 = d.sheet_wfirst[s] * kWarpsPerEntry, p1 = d.sheet_wfirst[s + 1] * kWarpsPerEntry;
+  double acc = 0.0;
+  for (int q = p0 + lane; q < p1; q += 32) acc += part[q];
+  acc = warp_sum(acc);
+  return __shfl_sync(0xffffffffu, acc, 0);
+}
+
+// Per sheet after k_cg_init: rz, rr, bb; a sheet with b = 0 (or non-finite) is done at once.
+template <class R>
+__global__ void k_cg_scalar_init(Dev<R> d, int phase) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= d.S) return;
+  const double rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
+  if ((threadIdx.x & 31) != 0) return;
+  CGSheet& c = d.cg[s];
+  c.rz = rz;
+  c.rr = rr;
+  c.bb = rr;
+  c.beta = 0.0;
+  c.iters = 0;
+  c.done = 0;
+  bool fin = false;
+  if (!isfinite(rr)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    fin = true;
+  } else if (rr == 0.0 || sqrt(rr) <= d.tol * sqrt(rr)) {
+    fin = true;
+  }
+  if (fin) finish_sheet(d, s, phase, 0, 0);
+}
+
+// Ap = A p_k (SELL-32 3x3 blocks, difference form); warp partials of p.Ap.
 template <class R, bool FUSED>
-__global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
-                                                      int use_cond) {
+__global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
+  const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
     const int s = d.work_sheet[w];
     if (d.cg[s].done) continue;  // uniform over the CTA
@@ -657,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
     R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const bool on = threadIdx.x < d.work_rows[w];
     const int i = d.work_row0[w] + threadIdx.x;
-    double v[1] = {0.0};
+    double v = 0.0;
     if (on) {
       const int sl = i >> 5, lane = i & 31;
       const int K = d.slice_K[sl], base = d.slice_base[sl];
@@ -706,47 +700,37 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d, int phase, cudaG
         y.z += lds(a + 192) * d0.x + lds(a + 224) * d0.y + lds(a + 256) * d0.z;
       }
       st3(d.Ap, i, y);
-      v[0] = rdot3(pi, y);
+      v = rdot3(pi, y);
     }
-    double tot[1];
-    if (sheet_reduce<1>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
-      CGSheet& c = d.cg[s];
-      c.pAp = tot[0];
-      if (!isfinite(tot[0])) {
-        c.status |= CLOTH_STATUS_NONFINITE;
-        finish_sheet(d, s, phase, cond, use_cond);
-      } else if (tot[0] <= 0.0) {
-        c.status |= CLOTH_STATUS_INDEFINITE;
-        finish_sheet(d, s, phase, cond, use_cond);
-      } else {
-        c.alpha = c.rz / tot[0];
-      }
-    }
+    v = warp_sum(v);
+    if (lane_w == 0) d.part_a[(size_t)w * kWarpsPerEntry + wp] = v;
   }
 }
 
-// p_{k+1} = z_{k+1} + beta_{k+1} p_k (unfused schedule), after the update of iteration k
+// Per sheet: pAp, alpha = rz / pAp; p.Ap <= 0 or non-finite ends the sheet's solve.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
-  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
-    const int s = d.work_sheet[w];
-    if (d.cg[s].done) continue;
-    if (threadIdx.x >= d.work_rows[w]) continue;
-    const int k = d.cg[s].iters;  // already k + 1 after the update
-    const R beta = (R)d.cg[s].beta;
-    const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
-    R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
-    const int i = d.work_row0[w] + threadIdx.x;
-    stp(pnew, i, next_dir(ld3(d.z, i), beta, ldp(pold, i)));
+__global__ void k_cg_scalar_alpha(Dev<R> d, int phase, cudaGraphConditionalHandle cond, int use_cond) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= d.S || d.cg[s].done) return;  // uniform over the warp
+  const double pAp = sheet_sum(d, d.part_a, s);
+  if ((threadIdx.x & 31) != 0) return;
+  CGSheet& c = d.cg[s];
+  c.pAp = pAp;
+  if (!isfinite(pAp)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    finish_sheet(d, s, phase, cond, use_cond);
+  } else if (pAp <= 0.0) {
+    c.status |= CLOTH_STATUS_INDEFINITE;
+    finish_sheet(d, s, phase, cond, use_cond);
+  } else {
+    c.alpha = c.rz / pAp;
   }
 }
 
-// dv += alpha p_k (FP64), r -= alpha Ap, z = D^{-1} r (stored); rz, rr; beta; convergence.
-// Also counts the loop-body executions of this phase.
+// dv += alpha p_k (FP64), r -= alpha Ap, z = D^{-1} r (stored); warp partials of r.z, r.r.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cudaGraphConditionalHandle cond,
-                                                        int use_cond) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.body_runs[phase] += 1ull;
+__global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d) {
+  const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
     const int s = d.work_sheet[w];
     if (d.cg[s].done) continue;
@@ -754,39 +738,69 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d, int phase, cud
     const R* __restrict__ pk = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const bool on = threadIdx.x < d.work_rows[w];
     const int i = d.work_row0[w] + threadIdx.x;
-    const R alpha = (R)d.cg[s].alpha;
-    double v[2] = {0.0, 0.0};
+    const double al = d.cg[s].alpha;
+    const R alpha = (R)al;
+    double v0 = 0.0, v1 = 0.0;
     if (on) {
       const V3<R> p = ldp(pk, i), Ap = ld3(d.Ap, i);
       V3<double> x = ld3(d.dv, i);
       V3<R> r = ld3(d.r, i);
-      const double al = d.cg[s].alpha;
       x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
       r = axpy3(-alpha, Ap, r);
       st3(d.dv, i, x);
       st3(d.r, i, r);
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
       st3(d.z, i, z);
-      v[0] = rdot3(r, z);
-      v[1] = rdot3(r, r);
+      v0 = rdot3(r, z);
+      v1 = rdot3(r, r);
     }
-    double tot[2];
-    if (sheet_reduce<2>(v, w, s, d.sheet_wfirst, d.part, d.cnt, tot) && threadIdx.x == 0) {
-      CGSheet& c = d.cg[s];
-      c.beta = tot[0] / c.rz;
-      c.rz = tot[0];
-      c.rr = tot[1];
-      c.iters += 1;
-      if (!isfinite(tot[1]) || !isfinite(tot[0])) {
-        c.status |= CLOTH_STATUS_NONFINITE;
-        finish_sheet(d, s, phase, cond, use_cond);
-      } else if (sqrt(tot[1]) <= d.tol * sqrt(c.bb)) {
-        finish_sheet(d, s, phase, cond, use_cond);
-      } else if (c.iters >= d.maxit) {
-        c.status |= CLOTH_STATUS_CG_MAXITER;
-        finish_sheet(d, s, phase, cond, use_cond);
-      }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane_w == 0) {
+      d.part_a[(size_t)w * kWarpsPerEntry + wp] = v0;
+      d.part_b[(size_t)w * kWarpsPerEntry + wp] = v1;
     }
+  }
+}
+
+// Per sheet: beta = rz_new / rz, iteration count, convergence |r| <= tol |b|, max_iter.
+// Also counts the loop-body executions of this phase.
+template <class R>
+__global__ void k_cg_scalar_beta(Dev<R> d, int phase, cudaGraphConditionalHandle cond, int use_cond) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.body_runs[phase] += 1ull;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= d.S || d.cg[s].done) return;
+  const double rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
+  if ((threadIdx.x & 31) != 0) return;
+  CGSheet& c = d.cg[s];
+  c.beta = rz / c.rz;
+  c.rz = rz;
+  c.rr = rr;
+  c.iters += 1;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    finish_sheet(d, s, phase, cond, use_cond);
+  } else if (sqrt(rr) <= d.tol * sqrt(c.bb)) {
+    finish_sheet(d, s, phase, cond, use_cond);
+  } else if (c.iters >= d.maxit) {
+    c.status |= CLOTH_STATUS_CG_MAXITER;
+    finish_sheet(d, s, phase, cond, use_cond);
+  }
+}
+
+// p_{k+1} = z_{k+1} + beta_{k+1} p_k (separate-direction schedule), after k_cg_scalar_beta
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
+  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
+    const int s = d.work_sheet[w];
+    if (d.cg[s].done) continue;
+    if (threadIdx.x >= d.work_rows[w]) continue;
+    const int k = d.cg[s].iters;  // already k + 1
+    const R beta = (R)d.cg[s].beta;
+    const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
+    R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
+    const int i = d.work_row0[w] + threadIdx.x;
+    stp(pnew, i, next_dir(ld3(d.z, i), beta, ldp(pold, i)));
   }
 }
 

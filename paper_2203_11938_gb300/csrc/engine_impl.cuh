@@ -133,8 +133,8 @@ class Engine final : public EngineBase {
     d.Ap = alloc<R>(n3, &rc);
     d.dv = alloc<double>(n3, &rc);
     d.cg = alloc<CGSheet>(L_.S, &rc);
-    d.cnt = alloc<int>(L_.S, &rc);
-    d.part = alloc<double>(2 * (size_t)d.NW, &rc);
+    d.part_a = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
+    d.part_b = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.active = alloc<int>(1, &rc);
     d.iter_total = alloc<unsigned long long>(3, &rc);
     d.body_runs = alloc<unsigned long long>(3, &rc);
@@ -161,8 +161,7 @@ class Engine final : public EngineBase {
       *err = "device allocation failed";
       return rc;
     }
-    if (cudaMemset(d.cnt, 0, sizeof(int) * L_.S) != cudaSuccess ||
-        cudaMemset(d.cg, 0, sizeof(CGSheet) * L_.S) != cudaSuccess ||
+    if (cudaMemset(d.cg, 0, sizeof(CGSheet) * L_.S) != cudaSuccess ||
         cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
         cudaMemset(d.body_runs, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
         cudaEventCreate(&ev0_) != cudaSuccess || cudaEventCreate(&ev1_) != cudaSuccess ||
@@ -176,7 +175,7 @@ class Engine final : public EngineBase {
     int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R, true>, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R, false>, kThreads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_update<R>, kThreads, 0) != cudaSuccess) {
       *err = "CUDA occupancy query failed";
       return CLOTH_ERR_CUDA;
@@ -260,7 +259,7 @@ class Engine final : public EngineBase {
     if (fwd) *fwd = (int64_t)h[0];
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
-    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + (sched_fused_ ? 2 : 3) * (int64_t)(b[0] + b[1] + b[2]);
+    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + (sched_fused_ ? 4 : 5) * (int64_t)(b[0] + b[1] + b[2]);
     return CLOTH_OK;
   }
 
@@ -290,10 +289,10 @@ class Engine final : public EngineBase {
     auto one = [&]() {
       switch (which) {
         case 0:
-          if (sched_fused_) k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0);
-          else k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0);
+          if (sched_fused_) k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, st>>>(d_);
+          else k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, st>>>(d_);
           break;
-        case 1: k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_, kPhaseForward, 0, 0); break;
+        case 1: k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_); break;
         case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr); break;
         case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
         default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
@@ -500,15 +499,15 @@ class Engine final : public EngineBase {
     cg_grid_ = (schedule_ & 1) ? resident_grid_ : d_.NW;
   }
 
+  int scalar_grid() const { return (L_.S * 32 + 255) / 256; }
+
   void emit_cg_body(cudaStream_t s, int phase, cudaGraphConditionalHandle cond, int use_cond) {
-    if (sched_fused_) {
-      k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
-      k_cg_update<R><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
-    } else {
-      k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
-      k_cg_update<R><<<cg_grid_, kThreads, 0, s>>>(d_, phase, cond, use_cond);
-      k_cg_dir<R><<<cg_grid_, kThreads, 0, s>>>(d_);
-    }
+    if (sched_fused_) k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, s>>>(d_);
+    else k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, s>>>(d_);
+    k_cg_scalar_alpha<R><<<scalar_grid(), 256, 0, s>>>(d_, phase, cond, use_cond);
+    k_cg_update<R><<<cg_grid_, kThreads, 0, s>>>(d_);
+    k_cg_scalar_beta<R><<<scalar_grid(), 256, 0, s>>>(d_, phase, cond, use_cond);
+    if (!sched_fused_) k_cg_dir<R><<<cg_grid_, kThreads, 0, s>>>(d_);
   }
 
   static std::string tune_cache_path() {
@@ -594,7 +593,8 @@ class Engine final : public EngineBase {
     for (int sched = 0; sched < 4; ++sched) {
       set_schedule(sched);
       k_solve_begin<R><<<1, 32, 0, st>>>(d_);
-      k_cg_init<R><<<cg_grid_, kThreads, 0, st>>>(d_, d_.bvec, kPhaseForward);
+      k_cg_init<R><<<cg_grid_, kThreads, 0, st>>>(d_, d_.bvec);
+      k_cg_scalar_init<R><<<scalar_grid(), 256, 0, st>>>(d_, kPhaseForward);
       emit_cg_body(st, kPhaseForward, 0, 0);  // warm-up
       CLOTH_CUDA(cudaEventRecord(ev0_, st));
       for (int k = 0; k < iters; ++k) emit_cg_body(st, kPhaseForward, 0, 0);
@@ -622,7 +622,8 @@ class Engine final : public EngineBase {
   // conditional WHILE node whose condition the kernels clear when the last sheet ends.
   int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
     launch(k_solve_begin<R>, dim3(1), dim3(32), st, d_);
-    launch(k_cg_init<R>, dim3(cg_grid_), dim3(kThreads), st, d_, rhs, phase);
+    launch(k_cg_init<R>, dim3(cg_grid_), dim3(kThreads), st, d_, rhs);
+    launch(k_cg_scalar_init<R>, dim3(scalar_grid()), dim3(256), st, d_, phase);
     CLOTH_CUDA(cudaGetLastError());
     if (capturing) {
       cudaStreamCaptureStatus cs;
