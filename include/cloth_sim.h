@@ -88,8 +88,9 @@ typedef struct cloth_opts {
                                -1 = autotune at cloth_batch_create (times each schedule
                                on the batch's matrix, caches the choice in the JSON file
                                $CLOTH_TUNE_CACHE or ~/.cache/cloth_sim/tune.json);
-                               0..3: bit 1 = direction update folded into the SpMV,
-                               bit 0 = resident-CTA grid looping over rows             */
+                               0..7: bit 1 = direction update folded into the SpMV,
+                               bit 0 = resident-CTA grid looping over rows, bit 2 =
+                               cluster tail solver for the last few sheets             */
 } cloth_opts;
 
 #define CLOTH_PRECOND_JACOBI 0

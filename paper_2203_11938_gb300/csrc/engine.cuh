@@ -13,6 +13,7 @@
 //   Y_bar += lam^T (h f_mem - h^2 H~_mem u) / Y, kb_bar likewise, rho_bar += lam^T M_1 (h g - dv).
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,7 +65,9 @@ struct Dev {
   R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
   double* dv;  // CG solution (dv, or lambda in the adjoint), accumulated in FP64
   CGSheet* cg;
-  double *part_a, *part_b;  // per-warp partial sums [NW * 8]
+  double *part_a, *part_b, *part_c;  // per-warp partial sums [NW * 8] (r.z, r.r, p.Ap)
+  int* tail_list;                     // sheets handed to the cluster tail solver, [S + 1] (count last)
+  int tail_threshold;                 // the device loop hands over when <= this many sheets remain
   int* active;
   unsigned long long* iter_total;
   unsigned long long* body_runs;  // [3] CG loop-body executions per phase
@@ -155,7 +158,9 @@ __device__ __forceinline__ void finish_sheet(const Dev<R>& d, int s, int phase, 
   d.cg[s].done = 1;
   atomicAdd(&d.iter_total[phase], (unsigned long long)d.cg[s].iters);
   const int left = atomicSub(d.active, 1) - 1;
-  if (left == 0 && use_cond) cudaGraphSetConditional(cond, 0);
+  // exactly one thread sees each value of `left`: the one reaching the hand-over point
+  // ends the device loop (the cluster tail solver finishes the remaining sheets)
+  if (left == d.tail_threshold && use_cond) cudaGraphSetConditional(cond, 0);
 }
 
 // ------------------------------------------------------------------ layout moves
@@ -551,7 +556,7 @@ __global__ void k_solve_begin(Dev<R> d) {
 
 template <class R>
 __global__ void k_cond_set(Dev<R> d, cudaGraphConditionalHandle cond) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, *d.active > 0 ? 1u : 0u);
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, *d.active > d.tail_threshold ? 1u : 0u);
 }
 
 // Jacobi-PCG over all sheets at once.  The streaming kernels (init, SpMV, update,
@@ -638,7 +643,84 @@ __global__ void k_cg_scalar_init(Dev<R> d, int phase) {
   if (fin) finish_sheet(d, s, phase, 0, 0);
 }
 
-// Ap = A p_k (SELL-32 3x3 blocks, difference form); warp partials of p.Ap.
+// One row of the SpMV: Ap_i = (A p_k)_i in difference form; returns p_i . Ap_i (or 0).
+template <class R, bool FUSED>
+__device__ __forceinline__ double spmv_row(const Dev<R>& d, int i, R beta, const R* __restrict__ pold,
+                                           R* __restrict__ pnew) {
+  const int sl = i >> 5, lane = i & 31;
+  const int K = d.slice_K[sl], base = d.slice_base[sl];
+  V3<R> pi;
+  if (FUSED) {
+    pi = next_dir(ld3(d.z, i), beta, ldp(pold, i));
+    stp(pnew, i, pi);
+  } else {
+    pi = ldp(pnew, i);
+  }
+  const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
+  V3<R> y = {lds(a0) * pi.x + lds(a0 + 32) * pi.y + lds(a0 + 64) * pi.z,
+             lds(a0 + 96) * pi.x + lds(a0 + 128) * pi.y + lds(a0 + 160) * pi.z,
+             lds(a0 + 192) * pi.x + lds(a0 + 224) * pi.y + lds(a0 + 256) * pi.z};
+  int q = 1;
+  for (; q + 1 < K; q += 2) {  // two slots per iteration: more loads in flight
+    const int e0 = (base + q) * 32 + lane, e1 = e0 + 32;
+    const int j0 = lds(d.cols + e0), j1 = lds(d.cols + e1);
+    const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
+    const R* b = a + 32 * 9;
+    R av[9], bv[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      av[t] = lds(a + 32 * t);
+      bv[t] = lds(b + 32 * t);
+    }
+    const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
+    const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ldp(pold, j1)) : ldp(pnew, j1);
+    const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
+    const V3<R> d1 = {p1.x - pi.x, p1.y - pi.y, p1.z - pi.z};
+    y.x += av[0] * d0.x + av[1] * d0.y + av[2] * d0.z;
+    y.y += av[3] * d0.x + av[4] * d0.y + av[5] * d0.z;
+    y.z += av[6] * d0.x + av[7] * d0.y + av[8] * d0.z;
+    y.x += bv[0] * d1.x + bv[1] * d1.y + bv[2] * d1.z;
+    y.y += bv[3] * d1.x + bv[4] * d1.y + bv[5] * d1.z;
+    y.z += bv[6] * d1.x + bv[7] * d1.y + bv[8] * d1.z;
+  }
+  if (q < K) {
+    const int e0 = (base + q) * 32 + lane;
+    const int j0 = lds(d.cols + e0);
+    const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
+    const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
+    const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
+    y.x += lds(a) * d0.x + lds(a + 32) * d0.y + lds(a + 64) * d0.z;
+    y.y += lds(a + 96) * d0.x + lds(a + 128) * d0.y + lds(a + 160) * d0.z;
+    y.z += lds(a + 192) * d0.x + lds(a + 224) * d0.y + lds(a + 256) * d0.z;
+  }
+  st3(d.Ap, i, y);
+  return rdot3(pi, y);
+}
+
+// One row of the update: dv += alpha p_k (FP64), r -= alpha Ap, z = D^{-1} r (stored).
+template <class R>
+__device__ __forceinline__ void update_row(const Dev<R>& d, int i, double al, const R* __restrict__ pk, double& rz,
+                                           double& rr) {
+  const R alpha = (R)al;
+  const V3<R> p = ldp(pk, i), Ap = ld3(d.Ap, i);
+  V3<double> x = ld3(d.dv, i);
+  V3<R> r = ld3(d.r, i);
+  x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
+  r = axpy3(-alpha, Ap, r);
+  st3(d.dv, i, x);
+  st3(d.r, i, r);
+  const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
+  st3(d.z, i, z);
+  rz = rdot3(r, z);
+  rr = rdot3(r, r);
+}
+
+template <class R>
+__device__ __forceinline__ const R* pbuf(const Dev<R>& d, int parity) {
+  return d.p + PStride<R>::v * (size_t)d.Np * (parity & 1);
+}
+
+// Ap = A p_k over all active sheets; warp partials of p.Ap.
 template <class R, bool FUSED>
 __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
   const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -647,63 +729,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
     if (d.cg[s].done) continue;  // uniform over the CTA
     const int k = d.cg[s].iters;
     const R beta = (R)d.cg[s].beta;
-    const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
-    R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
-    const bool on = threadIdx.x < d.work_rows[w];
-    const int i = d.work_row0[w] + threadIdx.x;
     double v = 0.0;
-    if (on) {
-      const int sl = i >> 5, lane = i & 31;
-      const int K = d.slice_K[sl], base = d.slice_base[sl];
-      V3<R> pi;
-      if (FUSED) {
-        pi = next_dir(ld3(d.z, i), beta, ldp(pold, i));
-        stp(pnew, i, pi);
-      } else {
-        pi = ldp(pnew, i);
-      }
-      const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
-      V3<R> y = {lds(a0) * pi.x + lds(a0 + 32) * pi.y + lds(a0 + 64) * pi.z,
-                 lds(a0 + 96) * pi.x + lds(a0 + 128) * pi.y + lds(a0 + 160) * pi.z,
-                 lds(a0 + 192) * pi.x + lds(a0 + 224) * pi.y + lds(a0 + 256) * pi.z};
-      int q = 1;
-      for (; q + 1 < K; q += 2) {  // two slots per iteration: more loads in flight
-        const int e0 = (base + q) * 32 + lane, e1 = e0 + 32;
-        const int j0 = lds(d.cols + e0), j1 = lds(d.cols + e1);
-        const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
-        const R* b = a + 32 * 9;
-        R av[9], bv[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          av[t] = lds(a + 32 * t);
-          bv[t] = lds(b + 32 * t);
-        }
-        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
-        const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ldp(pold, j1)) : ldp(pnew, j1);
-        const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
-        const V3<R> d1 = {p1.x - pi.x, p1.y - pi.y, p1.z - pi.z};
-        y.x += av[0] * d0.x + av[1] * d0.y + av[2] * d0.z;
-        y.y += av[3] * d0.x + av[4] * d0.y + av[5] * d0.z;
-        y.z += av[6] * d0.x + av[7] * d0.y + av[8] * d0.z;
-        y.x += bv[0] * d1.x + bv[1] * d1.y + bv[2] * d1.z;
-        y.y += bv[3] * d1.x + bv[4] * d1.y + bv[5] * d1.z;
-        y.z += bv[6] * d1.x + bv[7] * d1.y + bv[8] * d1.z;
-      }
-      if (q < K) {
-        const int e0 = (base + q) * 32 + lane;
-        const int j0 = lds(d.cols + e0);
-        const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
-        const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
-        const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
-        y.x += lds(a) * d0.x + lds(a + 32) * d0.y + lds(a + 64) * d0.z;
-        y.y += lds(a + 96) * d0.x + lds(a + 128) * d0.y + lds(a + 160) * d0.z;
-        y.z += lds(a + 192) * d0.x + lds(a + 224) * d0.y + lds(a + 256) * d0.z;
-      }
-      st3(d.Ap, i, y);
-      v = rdot3(pi, y);
-    }
+    if (threadIdx.x < d.work_rows[w])
+      v = spmv_row<R, FUSED>(d, d.work_row0[w] + threadIdx.x, beta, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
     v = warp_sum(v);
-    if (lane_w == 0) d.part_a[(size_t)w * kWarpsPerEntry + wp] = v;
+    if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = v;
   }
 }
 
@@ -712,7 +742,7 @@ template <class R>
 __global__ void k_cg_scalar_alpha(Dev<R> d, int phase, cudaGraphConditionalHandle cond, int use_cond) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (s >= d.S || d.cg[s].done) return;  // uniform over the warp
-  const double pAp = sheet_sum(d, d.part_a, s);
+  const double pAp = sheet_sum(d, d.part_c, s);
   if ((threadIdx.x & 31) != 0) return;
   CGSheet& c = d.cg[s];
   c.pAp = pAp;
@@ -735,25 +765,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d) {
     const int s = d.work_sheet[w];
     if (d.cg[s].done) continue;
     const int k = d.cg[s].iters;
-    const R* __restrict__ pk = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
-    const bool on = threadIdx.x < d.work_rows[w];
-    const int i = d.work_row0[w] + threadIdx.x;
-    const double al = d.cg[s].alpha;
-    const R alpha = (R)al;
     double v0 = 0.0, v1 = 0.0;
-    if (on) {
-      const V3<R> p = ldp(pk, i), Ap = ld3(d.Ap, i);
-      V3<double> x = ld3(d.dv, i);
-      V3<R> r = ld3(d.r, i);
-      x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
-      r = axpy3(-alpha, Ap, r);
-      st3(d.dv, i, x);
-      st3(d.r, i, r);
-      const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
-      st3(d.z, i, z);
-      v0 = rdot3(r, z);
-      v1 = rdot3(r, r);
-    }
+    if (threadIdx.x < d.work_rows[w]) update_row(d, d.work_row0[w] + threadIdx.x, d.cg[s].alpha, pbuf(d, k), v0, v1);
     v0 = warp_sum(v0);
     v1 = warp_sum(v1);
     if (lane_w == 0) {
@@ -801,6 +814,114 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
     R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const int i = d.work_row0[w] + threadIdx.x;
     stp(pnew, i, next_dir(ld3(d.z, i), beta, ldp(pold, i)));
+  }
+}
+
+// ------------------------------------------------------------------ cluster tail solver
+// When only a few sheets are still iterating, the device loop above pays a full set of
+// launches per iteration for little work.  The tail solver gives each remaining sheet
+// one thread-block cluster of kTailCluster CTAs that runs the rest of its CG without
+// returning: the same row kernels and the same per-warp partial sums as the loop, with
+// the two reductions of an iteration separated by hardware cluster barriers
+// (release/acquire at cluster scope), so its results are bitwise those of the loop.
+// Every CTA of a cluster derives alpha, beta and the stopping test from the same
+// partials, so all take the same branches; the loop ends at convergence, on a bad
+// scalar or at max_iter.
+constexpr int kTailCluster = 8;
+
+template <class R>
+__global__ void k_tail_prep(Dev<R> d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int n = 0;
+    for (int s = 0; s < d.S; ++s)
+      if (!d.cg[s].done) d.tail_list[n++] = s;
+    d.tail_list[d.S] = n;
+  }
+}
+
+template <class R>
+__global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads) k_cg_tail(Dev<R> d, int phase) {
+  namespace cgrp = cooperative_groups;
+  cgrp::cluster_group cl = cgrp::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int cid = blockIdx.x / kTailCluster;
+  if (cid >= d.tail_list[d.S]) return;  // uniform over the cluster
+  const int s = d.tail_list[cid];
+  __shared__ double sh[3];
+  const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int w0 = d.sheet_wfirst[s], w1 = d.sheet_wfirst[s + 1];
+  int k = d.cg[s].iters;
+  double rz = d.cg[s].rz, beta = d.cg[s].beta, rr = d.cg[s].rr, pAp = 0.0, al = 0.0;
+  const double bb = d.cg[s].bb;
+  int status = 0;
+  while (true) {
+    for (int w = w0 + rank; w < w1; w += kTailCluster) {
+      double v = 0.0;
+      if (threadIdx.x < d.work_rows[w])
+        v = spmv_row<R, true>(d, d.work_row0[w] + threadIdx.x, (R)beta, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
+      v = warp_sum(v);
+      if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = v;
+    }
+    cl.sync();
+    if (threadIdx.x < 32) {
+      const double t = sheet_sum(d, d.part_c, s);
+      if (threadIdx.x == 0) sh[0] = t;
+    }
+    __syncthreads();
+    pAp = sh[0];
+    if (!isfinite(pAp)) {
+      status |= CLOTH_STATUS_NONFINITE;
+      break;
+    }
+    if (pAp <= 0.0) {
+      status |= CLOTH_STATUS_INDEFINITE;
+      break;
+    }
+    al = rz / pAp;
+    for (int w = w0 + rank; w < w1; w += kTailCluster) {
+      double v0 = 0.0, v1 = 0.0;
+      if (threadIdx.x < d.work_rows[w]) update_row(d, d.work_row0[w] + threadIdx.x, al, pbuf(d, k), v0, v1);
+      v0 = warp_sum(v0);
+      v1 = warp_sum(v1);
+      if (lane_w == 0) {
+        d.part_a[(size_t)w * kWarpsPerEntry + wp] = v0;
+        d.part_b[(size_t)w * kWarpsPerEntry + wp] = v1;
+      }
+    }
+    cl.sync();
+    if (threadIdx.x < 32) {
+      const double a = sheet_sum(d, d.part_a, s), b = sheet_sum(d, d.part_b, s);
+      if (threadIdx.x == 0) {
+        sh[1] = a;
+        sh[2] = b;
+      }
+    }
+    __syncthreads();
+    const double rz_new = sh[1];
+    rr = sh[2];
+    beta = rz_new / rz;
+    rz = rz_new;
+    k += 1;
+    if (!isfinite(rr) || !isfinite(rz_new)) {
+      status |= CLOTH_STATUS_NONFINITE;
+      break;
+    }
+    if (sqrt(rr) <= d.tol * sqrt(bb)) break;
+    if (k >= d.maxit) {
+      status |= CLOTH_STATUS_CG_MAXITER;
+      break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    CGSheet& c = d.cg[s];
+    c.iters = k;
+    c.rz = rz;
+    c.rr = rr;
+    c.beta = beta;
+    c.alpha = al;
+    c.pAp = pAp;
+    c.status |= status;
+    finish_sheet(d, s, phase, 0, 0);
   }
 }
 

@@ -135,6 +135,8 @@ class Engine final : public EngineBase {
     d.cg = alloc<CGSheet>(L_.S, &rc);
     d.part_a = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.part_b = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
+    d.part_c = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
+    d.tail_list = alloc<int>((size_t)L_.S + 1, &rc);
     d.active = alloc<int>(1, &rc);
     d.iter_total = alloc<unsigned long long>(3, &rc);
     d.body_runs = alloc<unsigned long long>(3, &rc);
@@ -182,6 +184,26 @@ class Engine final : public EngineBase {
     }
     cg_grid_ = std::max(1, std::min(d.NW, sms * std::max(1, std::min(per_sm, per_sm2))));
     resident_grid_ = cg_grid_;
+    // tail solver: as many sheets as clusters can be resident at once, and only when every
+    // sheet is small enough for one cluster (<= 64 work entries = 16384 rows)
+    {
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(kTailCluster);
+      lc.blockDim = dim3(kThreads);
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = kTailCluster;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      lc.attrs = &at;
+      lc.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, k_cg_tail<R>, &lc) != cudaSuccess) clusters = 0;
+      int max_entries = 0;
+      for (int s2 = 0; s2 < L_.S; ++s2) max_entries = std::max(max_entries, L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2]);
+      tail_clusters_ = (max_entries <= 64) ? std::max(0, std::min(L_.S, clusters)) : 0;
+      cudaGetLastError();
+    }
     if (o_.cg_schedule >= 0) {
       set_schedule(o_.cg_schedule);
     } else {
@@ -494,9 +516,10 @@ class Engine final : public EngineBase {
   // SpMV (2 kernels per iteration) else a separate direction kernel (3); bit 0 = grid of
   // resident CTAs looping over work entries else one CTA per work entry.
   void set_schedule(int sched) {
-    schedule_ = sched & 3;
+    schedule_ = sched & 7;
     sched_fused_ = (schedule_ & 2) != 0;
     cg_grid_ = (schedule_ & 1) ? resident_grid_ : d_.NW;
+    d_.tail_threshold = (schedule_ & 4) ? tail_clusters_ : 0;
   }
 
   int scalar_grid() const { return (L_.S * 32 + 255) / 256; }
@@ -570,7 +593,7 @@ class Engine final : public EngineBase {
     auto cache = path.empty() ? std::map<std::string, int>() : read_tune_cache(path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-      set_schedule(it->second);
+      set_schedule((it->second & 3) | (tail_clusters_ > 0 ? 4 : 0));
       return CLOTH_OK;
     }
     cudaStream_t st = cap_stream_;
@@ -591,7 +614,7 @@ class Engine final : public EngineBase {
     int best_s = 3;
     const int iters = 12;
     for (int sched = 0; sched < 4; ++sched) {
-      set_schedule(sched);
+      set_schedule(sched);  // loop kernels only (bit 2, the tail solver, is set by eligibility)
       k_solve_begin<R><<<1, 32, 0, st>>>(d_);
       k_cg_init<R><<<cg_grid_, kThreads, 0, st>>>(d_, d_.bvec);
       k_cg_scalar_init<R><<<scalar_grid(), 256, 0, st>>>(d_, kPhaseForward);
@@ -607,6 +630,7 @@ class Engine final : public EngineBase {
         best_s = sched;
       }
     }
+    if (tail_clusters_ > 0) best_s |= 4;
     set_schedule(best_s);
     d_.material = mat_;
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
@@ -649,6 +673,7 @@ class Engine final : public EngineBase {
       cudaGraph_t out = nullptr;
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
+      emit_tail(st, phase);
       return CLOTH_OK;
     }
     const int poll = std::max(1, o_.cg_poll_every);
@@ -656,14 +681,23 @@ class Engine final : public EngineBase {
     while (true) {
       CLOTH_CUDA(cudaMemcpyAsync(host_active_, d_.active, sizeof(int), cudaMemcpyDeviceToHost, st));
       CLOTH_CUDA(cudaStreamSynchronize(st));
-      if (*host_active_ <= 0 || launched >= o_.cg_max_iter) break;
+      if (*host_active_ <= d_.tail_threshold || launched >= o_.cg_max_iter) break;
       for (int k = 0; k < poll; ++k) {
         emit_cg_body(st, phase, 0, 0);
       }
       launched += poll;
       CLOTH_CUDA(cudaGetLastError());
     }
+    emit_tail(st, phase);
+    CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
+  }
+
+  // the sheets still running after the device loop finish in the cluster tail solver
+  void emit_tail(cudaStream_t st, int phase) {
+    if (d_.tail_threshold <= 0) return;
+    launch(k_tail_prep<R>, dim3(1), dim3(32), st, d_);
+    launch(k_cg_tail<R>, dim3(kTailCluster * d_.tail_threshold), dim3(kThreads), st, d_, phase);
   }
 
   // One implicit step from (x, v) to (xn, vn); F: user-layout force row or null.
@@ -814,6 +848,7 @@ class Engine final : public EngineBase {
   std::vector<CachedGraph> graphs_;
   int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
   int cg_grid_ = 1;       // CTAs of the CG kernels (the schedule's choice)
+  int tail_clusters_ = 0; // sheets the cluster tail solver can take (0: not eligible)
   int resident_grid_ = 1; // CTAs resident at once on the whole GPU
   bool sched_fused_ = true;
   int schedule_ = 3;

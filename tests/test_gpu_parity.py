@@ -294,13 +294,15 @@ def test_batched_sheets_match_their_own_oracles(oracle_mod):
 
 
 def test_checkpointing_and_exec_modes_agree(oracle_mod):
-    """Checkpoint-and-recompute (C = 3 of 10 steps), the plain host-polled CG and all four
-    CG kernel schedules (and the autotuned one) give bitwise the same trajectory and
-    gradients as the captured-graph run without checkpoints."""
+    """Checkpoint-and-recompute (C = 3 of 10 steps), the plain host-polled CG and the CG
+    kernel schedules (fused or separate direction update, resident or per-entry grid,
+    with or without the cluster tail solver, and the autotuned one) give bitwise the same
+    trajectory and gradients as the captured-graph run without checkpoints."""
     sheets = sheets_mixed(seed=21)[:2]
     steps, dt = 10, 1 / 30
     res = []
-    for exec_mode, ckpt, sched in (("graph", 0, 3), ("graph", 3, 0), ("plain", 3, 1), ("plain", 0, 2), ("graph", 0, -1)):
+    for exec_mode, ckpt, sched in (("graph", 0, 3), ("graph", 3, 0), ("plain", 3, 1), ("plain", 0, 2), ("graph", 0, -1),
+                                   ("graph", 3, 6), ("plain", 0, 5), ("graph", 0, 4)):
         b = make_batch(sheets, steps=steps, dt=dt, precision="f32", tol=1e-6, exec_mode=exec_mode, ckpt=ckpt,
                        schedule=sched)
         x0 = to_cuda(np.concatenate([s.rest for s in sheets]), torch.float32)
