@@ -208,6 +208,31 @@ int cloth_spmv(cloth_batch* batch, const void* material, const void* x, const vo
 int cloth_third_contraction(cloth_batch* batch, const void* material, const void* x,
                             const void* a, const void* b, void* out, void* stream);
 
+/* ---- allocation-free variant (the paper has no counterpart) ----
+ *
+ * cloth_loss_l2_static computes exactly what cloth_loss_l2 computes (same kernels,
+ * per-sheet loss sum_{t=1..steps} sum_i |x_t^i - target_t^i|^2 in double and, when
+ * dL_dx is non-NULL, its gradient with row t = 0 set to 0) but needs no batch handle and
+ * never allocates device memory.  It is meant for callers that must not call
+ * cudaMalloc at the point of use: code running where another allocator owns the device
+ * memory (a framework that has reserved the whole pool), or latency-critical loops where
+ * the implicit device synchronisation of cudaMalloc/cudaFree would stall the pipeline.
+ * Its scratch (one double per sheet and time step) is a static array of 65,536 doubles
+ * (512 KiB) that every GPU loading this library holds until the process exits; calls
+ * with count * steps > 65,536 (or count or steps > 65,535) fail with
+ * CLOTH_ERR_INVALID_ARG.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array: calls whose kernels overlap on the
+ * GPU (e.g. issued to different streams without ordering) race and give wrong losses.
+ * count: sheets; sheet_offsets: device [count + 1] int32, vertex offset of each sheet in
+ * the packed user layout (sheet_offsets[count] = n_total); steps, n_total: as in
+ * cloth_loss_l2; precision: CLOTH_FP32 or CLOTH_FP64 (type of traj_x, target, dL_dx);
+ * traj_x, target: device [steps + 1][n_total][3]; loss: device [count] double;
+ * dL_dx: device [steps + 1][n_total][3] or NULL. */
+int cloth_loss_l2_static(int32_t count, const int32_t* sheet_offsets, int32_t steps, int32_t n_total,
+                         int32_t precision, const void* traj_x, const void* target, double* loss,
+                         void* dL_dx, void* stream);
+
 /* Thread-local description of the last error (empty string if none). */
 const char* cloth_last_error(void);
 

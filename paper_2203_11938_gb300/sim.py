@@ -31,7 +31,7 @@ EXPORTS = (
     "cloth_default_opts", "cloth_mesh_create", "cloth_mesh_destroy", "cloth_mesh_info", "cloth_batch_create",
     "cloth_batch_destroy", "cloth_batch_info", "cloth_forward", "cloth_backward", "cloth_loss_l2",
     "cloth_loss_pinhole", "cloth_stats", "cloth_internal_forces", "cloth_system_dense", "cloth_spmv",
-    "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel",
+    "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel", "cloth_loss_l2_static",
 )
 
 
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_system_dense.argtypes = [_vp] * 8
     lib.cloth_spmv.argtypes = [_vp] * 7
     lib.cloth_third_contraction.argtypes = [_vp] * 7
+    lib.cloth_loss_l2_static.argtypes = [ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                         _vp, _vp, _vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("cloth_default_opts", "cloth_last_error"):
