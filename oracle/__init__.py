@@ -58,6 +58,8 @@ def _load():
         lib.oracle_dihedral.argtypes = [_dp]
         lib.oracle_dihedral.restype = ctypes.c_double
         lib.oracle_system_dense.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_system_matvec.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp,
+                                             _dp, _dp, _dp, _dp]
         lib.oracle_forward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _ip]
         lib.oracle_forward.restype = ctypes.c_int
@@ -149,6 +151,15 @@ class OracleSim:
         self._lib.oracle_system_dense(self._h, _d(_f64(material)), float(eta), float(dt), _d(_f64(gravity)), _d(_f64(x)),
                                       _d(_f64(v)), _d(Fp), _d(A), _d(b))
         return A, b
+
+    def system_matvec(self, material, dt, gravity, x, v, F, p, eta=ETA):
+        """(A p, b) of one step at (x, v) with external force F (any size)."""
+        y = np.zeros((self.n, 3))
+        b = np.zeros((self.n, 3))
+        Fp = None if F is None else _f64(F)
+        self._lib.oracle_system_matvec(self._h, _d(_f64(material)), float(eta), float(dt), _d(_f64(gravity)),
+                                       _d(_f64(x)), _d(_f64(v)), _d(Fp), _d(_f64(p)), _d(y), _d(b))
+        return y, b
 
     # -- trajectory
     def forward(self, material, x0, v0, forces, *, dt, steps, tol, max_iter, gravity, eta=ETA, precond=PRECOND):

@@ -665,6 +665,33 @@ void oracle_system_dense(void* h, const double* material, double eta, double dt,
   }
 }
 
+// One step's system applied to a vector (any mesh size): y = A p and the right-hand
+// side b, with A = M + h^2 H~ and b = h (f + M g + F) - h^2 H~ v (pinned rows identity, b = 0).
+void oracle_system_matvec(void* h, const double* material, double eta, double dt, const double* gravity,
+                          const double* x, const double* v, const double* F, const double* p, double* y, double* b) {
+  const Sim* s = static_cast<Sim*>(h);
+  Mat mt{material[0], material[1], material[2], material[3], eta};
+  const int N = 3 * s->n;
+  Sparse Hm(N), Hb(N);
+  internal_hessian(*s, mt, x, Hm, Hb);
+  Sparse A = system_matrix(*s, mt, dt, Hm, Hb);
+  std::vector<double> pv(p, p + N), yv(N), fm(N), fb(N), Hv(N), Hv2(N), vv(v, v + N);
+  A.matvec(pv, yv);
+  std::copy(yv.begin(), yv.end(), y);
+  internal_forces(*s, mt, x, fm.data(), fb.data(), nullptr);
+  Hm.matvec(vv, Hv);
+  Hb.matvec(vv, Hv2);
+  for (int i = 0; i < N; ++i) {
+    const int vi = i / 3;
+    if (s->pinned[vi]) {
+      b[i] = 0.0;
+      continue;
+    }
+    double f = fm[i] + fb[i] + mt.rho * s->area3[vi] * gravity[i % 3] + (F ? F[i] : 0.0);
+    b[i] = dt * (f - dt * (Hv[i] + Hv2[i]));
+  }
+}
+
 // Forward trajectory.  x0, v0: [n][3]; forces: [steps][n][3] or NULL;
 // traj_x, traj_v: [steps+1][n][3]; dv_out [steps][n][3] or NULL; cg_iters [steps];
 // status: worst per-step solver status (0 ok, 1 maxiter, 2 indefinite, 3 non-finite).

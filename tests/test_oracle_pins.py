@@ -282,6 +282,20 @@ def test_pcg_matches_dense_solve(oracle_mod, precond):
     np.testing.assert_allclose(tx[1], x + dt * tv[1], rtol=0, atol=1e-15)
 
 
+def test_system_matvec_matches_dense_system(oracle_mod):
+    """The sparse one-step operator used for large-mesh checks equals the dense system."""
+    rng = np.random.default_rng(14)
+    sim, rest = _small_sheet(oracle_mod, 5, "top2")
+    x = rest + 0.02 * rng.normal(size=rest.shape)
+    v = 0.1 * rng.normal(size=rest.shape)
+    F = 1e-3 * rng.normal(size=rest.shape)
+    p = rng.normal(size=rest.shape)
+    A, b = sim.system_dense(MAT, 1 / 30, W.GRAVITY, x, v, F)
+    y, b2 = sim.system_matvec(MAT, 1 / 30, W.GRAVITY, x, v, F, p)
+    np.testing.assert_allclose(y.ravel(), A @ p.ravel(), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b2.ravel(), b, rtol=1e-12, atol=1e-16)
+
+
 def test_free_fall_closed_form(oracle_mod):
     """Unpinned sheet at rest, gravity only: K annihilates uniform motion, so
     dv = h g exactly, v_t = t h g and x_t = x_0 + h^2 g t (t+1)/2."""
