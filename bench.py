@@ -94,6 +94,22 @@ def units_per_step(wl):
     return wl.total_vertices * wl.steps
 
 
+def weak_scaling_value(units_local, steps, ms_local, dist=None, device="cpu"):
+    """Whole-job throughput: the units every rank processed over `steps` bench steps,
+    divided by the slowest rank's elapsed time.  Returns (value, ms_max, units_total)."""
+    import torch
+
+    t = torch.tensor([float(ms_local), float(units_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        ms = t[:1].clone()
+        un = t[1:].clone()
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(un, op=dist.ReduceOp.SUM)
+        t = torch.cat([ms, un])
+    ms_max, units_total = float(t[0].item()), float(t[1].item())
+    return units_total * steps / (ms_max / 1e3), ms_max, units_total
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -252,14 +268,10 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     log(f"timed region {ms:.1f} ms for {args.steps} steps")
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    units = units_per_step(wl)
+    value, ms_max, units_all = weak_scaling_value(units, args.steps, ms, dist, dev)
     stats = b.stats()
     status = int(st.max().item()) | int(g["status"].max().item())
-    units = units_per_step(wl)
-    value = units * world * args.steps / (ms_max / 1e3)
     launches_per_step = stats["kernel_launches"] + 2  # + the two loss kernels
 
     # -------------------- end to end through the public API with host buffers
@@ -305,10 +317,8 @@ def run_ours(args):
             e2e_step()
         a1.record(stream)
         torch.cuda.synchronize()
-        ems = torch.tensor([a0.elapsed_time(a1)], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
-        e2e = {"value": units * world * args.e2e_steps / (float(ems.item()) / 1e3), "unit": UNIT,
+        e2e_value, _, _ = weak_scaling_value(units, args.e2e_steps, a0.elapsed_time(a1), dist, dev)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
 
     log(f"e2e done {e2e}")
