@@ -251,6 +251,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         log(f"warm-up step done {b.stats()}")
     stats = b.stats()
+    per_sheet = {}
+    for ph in ("forward", "adjoint"):
+        mx, tot = b.sheet_iterations(ph)
+        # the loop runs as long as its slowest sheet: the largest per-sheet mean bounds a solve
+        per_sheet[ph] = {"mean": round(float(tot.sum()) / (wl.steps * len(wl.sheets)), 1),
+                         "slowest_sheet_mean": round(float(tot.max()) / wl.steps, 1),
+                         "largest_solve": int(mx.max())}
     sampler = ClockSampler(local)
     sampler.start()
     if dist:
@@ -395,6 +402,7 @@ def run_ours(args):
             "cg_iters_per_step": {"forward": stats["fwd_cg_iters"] / (wl.steps * len(wl.sheets)),
                                   "adjoint": stats["bwd_cg_iters"] / (wl.steps * len(wl.sheets)),
                                   "recompute": stats["recompute_cg_iters"] / (wl.steps * len(wl.sheets))},
+            "cg_iters_per_solve": per_sheet,
             "status_bits": status, "plain_single_sheet_gpu": plain,
             "batched_vs_plain": (value / world) / plain["value"] if plain else None,
         }

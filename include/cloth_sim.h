@@ -168,6 +168,14 @@ int cloth_loss_pinhole(cloth_batch* batch, const void* traj_x, const void* targe
 int cloth_stats(cloth_batch* batch, int64_t* fwd_cg_iters, int64_t* bwd_cg_iters,
                 int64_t* recompute_cg_iters, int64_t* kernel_launches);
 
+/* Per-sheet CG iteration counts of the last call of one phase: 0 = the solves of
+ * cloth_forward, 1 = the adjoint solves of cloth_backward, 2 = the forward solves
+ * cloth_backward recomputed from checkpoints.  max_iters (host [count]): the most
+ * iterations one solve of that sheet took; total_iters (host [count]): the sum over
+ * its solves.  Either may be NULL.  Synchronises the stream of the last call.
+ * Error INVALID_ARG for another phase. */
+int cloth_sheet_iterations(cloth_batch* batch, int32_t phase, int32_t* max_iters, int64_t* total_iters);
+
 /* Size of the step matrix A (Eq. 4-5) in 3x3 blocks: rows (vertices, each sheet
  * padded to a multiple of 32), blocks (structurally nonzero blocks) and
  * stored_blocks (blocks stored by the SELL-32 layout, padding included); cg_schedule:

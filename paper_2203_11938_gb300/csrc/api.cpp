@@ -158,6 +158,15 @@ int cloth_stats(cloth_batch* batch, int64_t* fwd, int64_t* bwd, int64_t* rec, in
   return batch->engine->stats(fwd, bwd, rec, launches);
 }
 
+int cloth_sheet_iterations(cloth_batch* batch, int32_t phase, int32_t* max_iters, int64_t* total_iters) {
+  CLOTH_NEED_BATCH("cloth_sheet_iterations");
+  if (phase < 0 || phase > 2) {
+    cloth::set_last_error("cloth_sheet_iterations: phase must be 0 (forward), 1 (adjoint) or 2 (recomputed forward)");
+    return CLOTH_ERR_INVALID_ARG;
+  }
+  return batch->engine->sheet_iterations(phase, max_iters, total_iters);
+}
+
 int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks, int64_t* stored_blocks,
                       int32_t* cg_schedule) {
   CLOTH_NEED_BATCH("cloth_matrix_info");

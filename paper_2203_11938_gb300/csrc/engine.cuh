@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -25,6 +26,7 @@
 
 #include "elements.cuh"
 #include "engine.h"
+#include "ffloat.cuh"
 
 namespace cloth {
 
@@ -33,6 +35,7 @@ constexpr int kElemThreads = 128;
 
 struct CGSheet {
   double rz, rr, bb, pAp, alpha, beta;
+  float alpha_hi, alpha_lo;  // alpha as a float-float (FP32 mode's solution update)
   int iters, done, status, pad;
 };
 
@@ -63,7 +66,8 @@ struct Dev {
   R *Aval, *bvec, *r, *z, *Ap;
   R* p;  // two direction buffers [2][Np][3] (p_k and p_{k-1})
   R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
-  double* dv;  // CG solution (dv, or lambda in the adjoint), accumulated in FP64
+  double* dv;  // CG solution (dv, or lambda in the adjoint): FP64 after each solve
+  float *dvh, *dvl;  // FP32 mode: the solution accumulated as float-float hi + lo [Np][3]
   CGSheet* cg;
   double *part_a, *part_b, *part_c;  // per-warp partial sums [NW * 8] (r.z, r.r, p.Ap)
   int* tail_list;                     // sheets handed to the cluster tail solver, [S + 1] (count last)
@@ -71,6 +75,7 @@ struct Dev {
   int* active;
   unsigned long long* iter_total;
   unsigned long long* body_runs;  // [3] CG loop-body executions per phase
+  unsigned* sheet_iters;          // [3][S][2] per phase and sheet: largest solve, sum over solves
   double* gacc;  // [S][3] dL/dY, dL/dkb, dL/drho
   // parameters
   R h, gx, gy, gz, eta;
@@ -118,6 +123,34 @@ template <class R> __device__ __forceinline__ double rdot3(V3<R> a, V3<R> b) {
   return (double)(a.x * b.x + a.y * b.y + a.z * b.z);
 }
 
+// CG dot-product accumulator of one thread: FP64 in FP64 mode; in FP32 mode a
+// float-float, so the in-warp sum runs on the FP32 pipe at FP64-like accuracy.  Each
+// warp's sum leaves as one double; sums over warps are FP64.
+template <class R> struct CGAcc { using T = double; };
+template <> struct CGAcc<float> { using T = FF; };
+template <class R> using acc_t = typename CGAcc<R>::T;
+
+template <class R> __device__ __forceinline__ acc_t<R> acc_zero() { return 0.0; }
+template <> __device__ __forceinline__ FF acc_zero<float>() { return {0.f, 0.f}; }
+template <class R> __device__ __forceinline__ acc_t<R> acc_dot3(V3<R> a, V3<R> b) { return rdot3(a, b); }
+template <> __device__ __forceinline__ FF acc_dot3<float>(V3<float> a, V3<float> b) {
+  return {a.x * b.x + a.y * b.y + a.z * b.z, 0.f};
+}
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+// warp sum, valid in lane 0, as a double
+__device__ __forceinline__ double acc_warp_total(double x) { return warp_sum(x); }
+__device__ __forceinline__ double acc_warp_total(FF x) { return ff_to_double(ff_warp_sum(x)); }
+
+// alpha of a sheet in the form the solution update takes
+template <class R> __device__ __forceinline__ acc_t<R> alpha_of(const CGSheet& c) { return c.alpha; }
+template <> __device__ __forceinline__ FF alpha_of<float>(const CGSheet& c) { return {c.alpha_hi, c.alpha_lo}; }
+__device__ __forceinline__ double alpha_cast(double a) { return a; }
+__device__ __forceinline__ float alpha_cast(FF a) { return a.hi; }  // = (float) alpha
+
 // z = D^{-1} r with the stored 3x3 inverse (SoA [9][Np])
 template <class R>
 __device__ __forceinline__ V3<R> apply_dinv(const R* __restrict__ D, int Np, int i, V3<R> r) {
@@ -157,6 +190,10 @@ __device__ __forceinline__ void finish_sheet(const Dev<R>& d, int s, int phase, 
                                              int use_cond) {
   d.cg[s].done = 1;
   atomicAdd(&d.iter_total[phase], (unsigned long long)d.cg[s].iters);
+  // one thread finishes sheet s of a solve, so these need no atomics
+  unsigned* si = d.sheet_iters + 2 * ((size_t)phase * d.S + s);
+  si[0] = max(si[0], (unsigned)d.cg[s].iters);
+  si[1] += (unsigned)d.cg[s].iters;
   const int left = atomicSub(d.active, 1) - 1;
   // exactly one thread sees each value of `left`: the one reaching the hand-over point
   // ends the device loop (the cluster tail solver finishes the remaining sheets)
@@ -571,12 +608,6 @@ __device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
   return {fma(beta, pold.x, z.x), fma(beta, pold.y, z.y), fma(beta, pold.z, z.z)};
 }
 
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return x;
-}
-
 // partial of warp `wp` (0..7) of work entry w: index w * 8 + wp
 constexpr int kWarpsPerEntry = kThreads / 32;
 
@@ -587,7 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
     const bool on = threadIdx.x < d.work_rows[w];
     const int i = d.work_row0[w] + threadIdx.x;
-    double v0 = 0.0, v1 = 0.0;
+    acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>();
     if (on) {
       const V3<R> r = ld3(rhs, i);
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
@@ -595,15 +626,19 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
       st3(d.z, i, z);
       stp(d.p, i, z);                                                          // p_0 (buffer 0)
       stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
-      st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
-      v0 = rdot3(r, z);
-      v1 = rdot3(r, r);
+      if constexpr (std::is_same<R, float>::value) {
+        st3(d.dvh, i, V3<float>{0.f, 0.f, 0.f});
+        st3(d.dvl, i, V3<float>{0.f, 0.f, 0.f});
+      } else {
+        st3(d.dv, i, V3<double>{0.0, 0.0, 0.0});
+      }
+      v0 = acc_dot3(r, z);
+      v1 = acc_dot3(r, r);
     }
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
+    const double t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
     if (lane == 0) {
-      d.part_a[(size_t)w * kWarpsPerEntry + wp] = v0;
-      d.part_b[(size_t)w * kWarpsPerEntry + wp] = v1;
+      d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
+      d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
     }
   }
 }
@@ -645,7 +680,7 @@ __global__ void k_cg_scalar_init(Dev<R> d, int phase) {
 
 // One row of the SpMV: Ap_i = (A p_k)_i in difference form; returns p_i . Ap_i (or 0).
 template <class R, bool FUSED>
-__device__ __forceinline__ double spmv_row(const Dev<R>& d, int i, R beta, const R* __restrict__ pold,
+__device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, const R* __restrict__ pold,
                                            R* __restrict__ pnew) {
   const int sl = i >> 5, lane = i & 31;
   const int K = d.slice_K[sl], base = d.slice_base[sl];
@@ -694,25 +729,44 @@ __device__ __forceinline__ double spmv_row(const Dev<R>& d, int i, R beta, const
     y.z += lds(a + 192) * d0.x + lds(a + 224) * d0.y + lds(a + 256) * d0.z;
   }
   st3(d.Ap, i, y);
-  return rdot3(pi, y);
+  return acc_dot3(pi, y);
 }
 
-// One row of the update: dv += alpha p_k (FP64), r -= alpha Ap, z = D^{-1} r (stored).
+// One row of the update: dv += alpha p_k (FP64, or float-float in FP32 mode),
+// r -= alpha Ap, z = D^{-1} r (stored).
 template <class R>
-__device__ __forceinline__ void update_row(const Dev<R>& d, int i, double al, const R* __restrict__ pk, double& rz,
-                                           double& rr) {
-  const R alpha = (R)al;
+__device__ __forceinline__ void update_row(const Dev<R>& d, int i, acc_t<R> al, const R* __restrict__ pk,
+                                           acc_t<R>& rz, acc_t<R>& rr) {
+  const R alpha = alpha_cast(al);
   const V3<R> p = ldp(pk, i), Ap = ld3(d.Ap, i);
-  V3<double> x = ld3(d.dv, i);
   V3<R> r = ld3(d.r, i);
-  x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
+  if constexpr (std::is_same<R, float>::value) {
+    const V3<float> xh = ld3(d.dvh, i), xl = ld3(d.dvl, i);
+    const FF a = ff_add({xh.x, xl.x}, ff_mul(al, p.x));
+    const FF b = ff_add({xh.y, xl.y}, ff_mul(al, p.y));
+    const FF c = ff_add({xh.z, xl.z}, ff_mul(al, p.z));
+    st3(d.dvh, i, V3<float>{a.hi, b.hi, c.hi});
+    st3(d.dvl, i, V3<float>{a.lo, b.lo, c.lo});
+  } else {
+    V3<double> x = ld3(d.dv, i);
+    x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
+    st3(d.dv, i, x);
+  }
   r = axpy3(-alpha, Ap, r);
-  st3(d.dv, i, x);
   st3(d.r, i, r);
   const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
   st3(d.z, i, z);
-  rz = rdot3(r, z);
-  rr = rdot3(r, r);
+  rz = acc_dot3(r, z);
+  rr = acc_dot3(r, r);
+}
+
+// FP32 mode: the solution as FP64, dv = hi + lo, once per solve.
+template <class R>
+__global__ void k_cg_solution(Dev<R> d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  const V3<float> h = ld3(d.dvh, i), l = ld3(d.dvl, i);
+  st3(d.dv, i, V3<double>{(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z});
 }
 
 template <class R>
@@ -729,11 +783,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
     if (d.cg[s].done) continue;  // uniform over the CTA
     const int k = d.cg[s].iters;
     const R beta = (R)d.cg[s].beta;
-    double v = 0.0;
+    acc_t<R> v = acc_zero<R>();
     if (threadIdx.x < d.work_rows[w])
       v = spmv_row<R, FUSED>(d, d.work_row0[w] + threadIdx.x, beta, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
-    v = warp_sum(v);
-    if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = v;
+    const double t = acc_warp_total(v);
+    if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = t;
   }
 }
 
@@ -754,6 +808,9 @@ __global__ void k_cg_scalar_alpha(Dev<R> d, int phase, cudaGraphConditionalHandl
     finish_sheet(d, s, phase, cond, use_cond);
   } else {
     c.alpha = c.rz / pAp;
+    const FF a = ff_from_double(c.alpha);
+    c.alpha_hi = a.hi;
+    c.alpha_lo = a.lo;
   }
 }
 
@@ -765,13 +822,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d) {
     const int s = d.work_sheet[w];
     if (d.cg[s].done) continue;
     const int k = d.cg[s].iters;
-    double v0 = 0.0, v1 = 0.0;
-    if (threadIdx.x < d.work_rows[w]) update_row(d, d.work_row0[w] + threadIdx.x, d.cg[s].alpha, pbuf(d, k), v0, v1);
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
+    acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>();
+    if (threadIdx.x < d.work_rows[w])
+      update_row(d, d.work_row0[w] + threadIdx.x, alpha_of<R>(d.cg[s]), pbuf(d, k), v0, v1);
+    const double t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
     if (lane_w == 0) {
-      d.part_a[(size_t)w * kWarpsPerEntry + wp] = v0;
-      d.part_b[(size_t)w * kWarpsPerEntry + wp] = v1;
+      d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
+      d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
     }
   }
 }
@@ -839,6 +896,9 @@ __global__ void k_tail_prep(Dev<R> d) {
   }
 }
 
+template <class R> __device__ __forceinline__ acc_t<R> acc_from_double(double x) { return x; }
+template <> __device__ __forceinline__ FF acc_from_double<float>(double x) { return ff_from_double(x); }
+
 template <class R>
 __global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads) k_cg_tail(Dev<R> d, int phase) {
   namespace cgrp = cooperative_groups;
@@ -847,70 +907,84 @@ __global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads)
   const int cid = blockIdx.x / kTailCluster;
   if (cid >= d.tail_list[d.S]) return;  // uniform over the cluster
   const int s = d.tail_list[cid];
-  __shared__ double sh[3];
+  // Thread 0 of each CTA forms the iteration's scalars (FP64) from the partial sums and
+  // hands the rest of the CTA only what the row kernels take, so no other thread does
+  // FP64 arithmetic.
+  __shared__ acc_t<R> bc_alpha;
+  __shared__ R bc_beta;
+  __shared__ int bc_stop;
   const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int w0 = d.sheet_wfirst[s], w1 = d.sheet_wfirst[s + 1];
   int k = d.cg[s].iters;
+  R beta_r = (R)d.cg[s].beta;
+  // thread 0's copy of the sheet's CG state
   double rz = d.cg[s].rz, beta = d.cg[s].beta, rr = d.cg[s].rr, pAp = 0.0, al = 0.0;
   const double bb = d.cg[s].bb;
   int status = 0;
   while (true) {
     for (int w = w0 + rank; w < w1; w += kTailCluster) {
-      double v = 0.0;
+      acc_t<R> v = acc_zero<R>();
       if (threadIdx.x < d.work_rows[w])
-        v = spmv_row<R, true>(d, d.work_row0[w] + threadIdx.x, (R)beta, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
-      v = warp_sum(v);
-      if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = v;
+        v = spmv_row<R, true>(d, d.work_row0[w] + threadIdx.x, beta_r, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
+      const double t = acc_warp_total(v);
+      if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = t;
     }
     cl.sync();
     if (threadIdx.x < 32) {
       const double t = sheet_sum(d, d.part_c, s);
-      if (threadIdx.x == 0) sh[0] = t;
+      if (threadIdx.x == 0) {
+        pAp = t;
+        int stop = 0;
+        if (!isfinite(pAp)) {
+          status |= CLOTH_STATUS_NONFINITE;
+          stop = 1;
+        } else if (pAp <= 0.0) {
+          status |= CLOTH_STATUS_INDEFINITE;
+          stop = 1;
+        } else {
+          al = rz / pAp;
+        }
+        bc_alpha = acc_from_double<R>(al);
+        bc_stop = stop;
+      }
     }
     __syncthreads();
-    pAp = sh[0];
-    if (!isfinite(pAp)) {
-      status |= CLOTH_STATUS_NONFINITE;
-      break;
-    }
-    if (pAp <= 0.0) {
-      status |= CLOTH_STATUS_INDEFINITE;
-      break;
-    }
-    al = rz / pAp;
+    if (bc_stop) break;
+    const acc_t<R> alpha = bc_alpha;
     for (int w = w0 + rank; w < w1; w += kTailCluster) {
-      double v0 = 0.0, v1 = 0.0;
-      if (threadIdx.x < d.work_rows[w]) update_row(d, d.work_row0[w] + threadIdx.x, al, pbuf(d, k), v0, v1);
-      v0 = warp_sum(v0);
-      v1 = warp_sum(v1);
+      acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>();
+      if (threadIdx.x < d.work_rows[w]) update_row(d, d.work_row0[w] + threadIdx.x, alpha, pbuf(d, k), v0, v1);
+      const double t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
       if (lane_w == 0) {
-        d.part_a[(size_t)w * kWarpsPerEntry + wp] = v0;
-        d.part_b[(size_t)w * kWarpsPerEntry + wp] = v1;
+        d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
+        d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
       }
     }
     cl.sync();
+    k += 1;
     if (threadIdx.x < 32) {
       const double a = sheet_sum(d, d.part_a, s), b = sheet_sum(d, d.part_b, s);
       if (threadIdx.x == 0) {
-        sh[1] = a;
-        sh[2] = b;
+        rr = b;
+        beta = a / rz;
+        rz = a;
+        int stop = 0;
+        if (!isfinite(rr) || !isfinite(a)) {
+          status |= CLOTH_STATUS_NONFINITE;
+          stop = 1;
+        } else if (sqrt(rr) <= d.tol * sqrt(bb)) {
+          stop = 1;
+        } else if (k >= d.maxit) {
+          status |= CLOTH_STATUS_CG_MAXITER;
+          stop = 1;
+        }
+        bc_beta = (R)beta;
+        bc_stop = stop;
       }
     }
     __syncthreads();
-    const double rz_new = sh[1];
-    rr = sh[2];
-    beta = rz_new / rz;
-    rz = rz_new;
-    k += 1;
-    if (!isfinite(rr) || !isfinite(rz_new)) {
-      status |= CLOTH_STATUS_NONFINITE;
-      break;
-    }
-    if (sqrt(rr) <= d.tol * sqrt(bb)) break;
-    if (k >= d.maxit) {
-      status |= CLOTH_STATUS_CG_MAXITER;
-      break;
-    }
+    if (bc_stop) break;
+    beta_r = bc_beta;
   }
   if (rank == 0 && threadIdx.x == 0) {
     CGSheet& c = d.cg[s];
@@ -919,6 +993,9 @@ __global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads)
     c.rr = rr;
     c.beta = beta;
     c.alpha = al;
+    const FF af = ff_from_double(al);
+    c.alpha_hi = af.hi;
+    c.alpha_lo = af.lo;
     c.pAp = pAp;
     c.status |= status;
     finish_sheet(d, s, phase, 0, 0);
@@ -945,7 +1022,11 @@ __global__ void k_state_update(Dev<R> d, const double* __restrict__ x, const dou
 template <class R>
 __global__ void k_reset_status(Dev<R> d, int phase) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < d.S) d.cg[s].status = 0;
+  if (s < d.S) {
+    d.cg[s].status = 0;
+    d.sheet_iters[2 * ((size_t)phase * d.S + s)] = 0;
+    d.sheet_iters[2 * ((size_t)phase * d.S + s) + 1] = 0;
+  }
   if (s == 0) {
     d.iter_total[phase] = 0;
     d.body_runs[phase] = 0;
@@ -1075,15 +1156,16 @@ __global__ void k_adj_vertex(Dev<R> d, double* __restrict__ ax, double* __restri
                              const double* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
-  V3<R> r1 = {R(0), R(0), R(0)}, r2 = {R(0), R(0), R(0)};
+  // element contributions are large and cancel at a vertex: summed in FP64
+  V3<double> r1 = {0.0, 0.0, 0.0}, r2 = {0.0, 0.0, 0.0};
   for (int q = d.vf_ptr[i]; q < d.vf_ptr[i + 1]; ++q) {
     const R* src = adj_slot(d, d.vf[q]);
-    r1.x += src[0];
-    r1.y += src[1];
-    r1.z += src[2];
-    r2.x += src[3];
-    r2.y += src[4];
-    r2.z += src[5];
+    r1.x += (double)src[0];
+    r1.y += (double)src[1];
+    r1.z += (double)src[2];
+    r2.x += (double)src[3];
+    r2.y += (double)src[4];
+    r2.z += (double)src[5];
   }
   const int u = d.i2u[i];
   const V3<double> a_x = ld3(ax, i), a_v = ld3(av, i), lam = ld3(d.dv, i);

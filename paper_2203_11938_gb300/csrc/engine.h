@@ -22,6 +22,7 @@ class EngineBase {
   virtual int loss_pinhole(const void* traj, const void* uv, const double* cam, double* loss, void* grad,
                            void* stream) = 0;
   virtual int stats(int64_t* fwd, int64_t* bwd, int64_t* rec, int64_t* launches) = 0;
+  virtual int sheet_iterations(int phase, int32_t* max_iters, int64_t* total_iters) = 0;
   virtual int matrix_info(int64_t* rows, int64_t* blocks, int64_t* slots, int32_t* schedule) = 0;
   virtual int time_kernel(int which, int reps, double* avg_ms, void* stream) = 0;
   virtual int internal_forces(const void* material, const void* x, void* fm, void* fb, void* stream) = 0;

@@ -132,6 +132,10 @@ class Engine final : public EngineBase {
     d.z = alloc<R>(n3, &rc);
     d.Ap = alloc<R>(n3, &rc);
     d.dv = alloc<double>(n3, &rc);
+    if (std::is_same<R, float>::value) {
+      d.dvh = alloc<float>(n3, &rc);
+      d.dvl = alloc<float>(n3, &rc);
+    }
     d.cg = alloc<CGSheet>(L_.S, &rc);
     d.part_a = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.part_b = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
@@ -140,6 +144,7 @@ class Engine final : public EngineBase {
     d.active = alloc<int>(1, &rc);
     d.iter_total = alloc<unsigned long long>(3, &rc);
     d.body_runs = alloc<unsigned long long>(3, &rc);
+    d.sheet_iters = alloc<unsigned>(6 * (size_t)L_.S, &rc);
     d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
     // the state (x, v) is carried in FP64 in both precisions
     seg_x_ = alloc<double>(n3 * (C_ + 1), &rc);
@@ -166,6 +171,7 @@ class Engine final : public EngineBase {
     if (cudaMemset(d.cg, 0, sizeof(CGSheet) * L_.S) != cudaSuccess ||
         cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
         cudaMemset(d.body_runs, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
+        cudaMemset(d.sheet_iters, 0, sizeof(unsigned) * 6 * L_.S) != cudaSuccess ||
         cudaEventCreate(&ev0_) != cudaSuccess || cudaEventCreate(&ev1_) != cudaSuccess ||
         cudaMallocHost(&host_active_, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking) != cudaSuccess ||
@@ -282,6 +288,18 @@ class Engine final : public EngineBase {
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
     if (launches) *launches = fixed_fwd_ + fixed_bwd_ + (sched_fused_ ? 4 : 5) * (int64_t)(b[0] + b[1] + b[2]);
+    return CLOTH_OK;
+  }
+
+  int sheet_iterations(int phase, int32_t* max_iters, int64_t* total_iters) override {
+    CLOTH_CUDA(cudaStreamSynchronize(last_stream_));
+    std::vector<unsigned> h(2 * (size_t)L_.S);
+    CLOTH_CUDA(cudaMemcpy(h.data(), d_.sheet_iters + 2 * (size_t)phase * L_.S, sizeof(unsigned) * h.size(),
+                          cudaMemcpyDeviceToHost));
+    for (int s = 0; s < L_.S; ++s) {
+      if (max_iters) max_iters[s] = (int32_t)h[2 * s];
+      if (total_iters) total_iters[s] = (int64_t)h[2 * s + 1];
+    }
     return CLOTH_OK;
   }
 
@@ -674,6 +692,7 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
       emit_tail(st, phase);
+      emit_solution(st);
       return CLOTH_OK;
     }
     const int poll = std::max(1, o_.cg_poll_every);
@@ -689,8 +708,14 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaGetLastError());
     }
     emit_tail(st, phase);
+    emit_solution(st);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
+  }
+
+  // FP32 mode accumulates the solution as float-float; its consumers read FP64
+  void emit_solution(cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value) launch(k_cg_solution<R>, dim3(grid_rows()), dim3(256), st, d_);
   }
 
   // the sheets still running after the device loop finish in the cluster tail solver
@@ -834,7 +859,7 @@ class Engine final : public EngineBase {
   BatchLayout L_;
   const void* fwd_forces_ = nullptr;  // force input of the last forward (the recompute reads it again)
   cloth_opts o_;
-  Dev<R> d_;
+  Dev<R> d_ = {};
   int T_ = 0, C_ = 0, nseg_ = 0, seg_valid_ = -1;
   bool have_forward_ = false;
   double *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;

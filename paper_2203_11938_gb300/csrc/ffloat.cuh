@@ -1,0 +1,59 @@
+// Float-float ("double-single") arithmetic on the FP32 pipe.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2, about 48
+// significant bits.  GB300 issues FP64 arithmetic at a small fraction of its FP32 rate, so
+// the FP32 mode's CG keeps its in-warp dot-product sums and its solution accumulator in
+// this form and turns to FP64 only once per warp (the partial sums, added over warps in
+// FP64) and once per solve (the solution vector).
+//
+// Addition: Knuth's two-sum of the high parts, the low parts added to its error, then a
+// fast two-sum renormalisation (Dekker 1971; the "sloppy" double-double addition of Hida,
+// Li and Bailey).  Product with a float: Dekker's exact product, its error term taken with
+// one fused multiply-add.  The explicit round-to-nearest intrinsics keep the compiler from
+// contracting or reassociating the error terms away.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cloth {
+
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+  const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, t);
+  return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+// a * x for a float-float a and a float x
+__device__ __forceinline__ FF ff_mul(FF a, float x) {
+  const float p = __fmul_rn(a.hi, x);
+  const float e = __fmaf_rn(a.hi, x, -p);  // exact: a.hi * x = p + e
+  const float t = __fmaf_rn(a.lo, x, e);
+  const float hi = __fadd_rn(p, t);
+  return {hi, __fsub_rn(t, __fsub_rn(hi, p))};
+}
+
+// nearest float-float of a double (hi is the double rounded to float)
+__host__ __device__ __forceinline__ FF ff_from_double(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ FF ff_warp_sum(FF x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const FF y = {__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+    x = ff_add(x, y);
+  }
+  return x;
+}
+
+}  // namespace cloth

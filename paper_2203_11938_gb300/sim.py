@@ -32,6 +32,7 @@ EXPORTS = (
     "cloth_batch_destroy", "cloth_batch_info", "cloth_forward", "cloth_backward", "cloth_loss_l2",
     "cloth_loss_pinhole", "cloth_stats", "cloth_internal_forces", "cloth_system_dense", "cloth_spmv",
     "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel", "cloth_loss_l2_static",
+    "cloth_sheet_iterations",
 )
 
 
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_loss_pinhole.argtypes = [_vp] * 7
     lib.cloth_stats.argtypes = [_vp] * 5
     lib.cloth_matrix_info.argtypes = [_vp] * 5
+    lib.cloth_sheet_iterations.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
     lib.cloth_time_kernel.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.cloth_internal_forces.argtypes = [_vp] * 6
     lib.cloth_system_dense.argtypes = [_vp] * 8
@@ -276,6 +278,19 @@ class ClothBatch:
                "cloth_stats")
         return {"fwd_cg_iters": f.value, "bwd_cg_iters": b.value, "recompute_cg_iters": r.value,
                 "kernel_launches": n.value}
+
+    PHASES = {"forward": 0, "adjoint": 1, "recompute": 2}
+
+    def sheet_iterations(self, phase="forward"):
+        """Per-sheet CG iterations of the last call of `phase`: (largest single solve,
+        sum over solves), each a numpy array [count]."""
+        import numpy as np
+
+        mx = np.zeros(self.count, np.int32)
+        tot = np.zeros(self.count, np.int64)
+        _check(_lib.cloth_sheet_iterations(self._h, self.PHASES[phase], mx.ctypes.data_as(_vp),
+                                           tot.ctypes.data_as(_vp)), "cloth_sheet_iterations")
+        return mx, tot
 
     def matrix_info(self):
         r, b, s, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
