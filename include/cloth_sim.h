@@ -90,7 +90,15 @@ typedef struct cloth_opts {
                                $CLOTH_TUNE_CACHE or ~/.cache/cloth_sim/tune.json);
                                0..7: bit 1 = direction update folded into the SpMV,
                                bit 0 = resident-CTA grid looping over rows, bit 2 =
-                               cluster tail solver for the last few sheets             */
+                               per-sheet cluster solver for the sheets still iterating
+                               at the hand-over point (every sheet of at most 8192
+                               vertices gets one thread-block cluster)               */
+  int32_t cg_handover;      /* with schedule bit 2: the device loop runs while more than
+                               this many sheets are still iterating, then the per-sheet
+                               solver finishes them (>= count: no loop at all);
+                               0 = chosen by the autotuner (cg_schedule = -1: timed
+                               whole solves of the loop alone and of hand-overs at
+                               count/16 ... count), or every sheet (explicit schedule) */
 } cloth_opts;
 
 #define CLOTH_PRECOND_JACOBI 0

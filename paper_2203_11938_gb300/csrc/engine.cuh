@@ -70,7 +70,6 @@ struct Dev {
   float *dvh, *dvl;  // FP32 mode: the solution accumulated as float-float hi + lo [Np][3]
   CGSheet* cg;
   double *part_a, *part_b, *part_c;  // per-warp partial sums [NW * 8] (r.z, r.r, p.Ap)
-  int* tail_list;                     // sheets handed to the cluster tail solver, [S + 1] (count last)
   int tail_threshold;                 // the device loop hands over when <= this many sheets remain
   int* active;
   unsigned long long* iter_total;
@@ -97,6 +96,29 @@ template <class R> __device__ __forceinline__ void st3(R* a, int i, V3<R> v) {
 }
 template <class R> __device__ __forceinline__ V3<R> add3(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 
+// Explicitly rounded operations for the CG row arithmetic: every kernel that computes a
+// CG row (the device loop and the per-sheet solver) evaluates it through these, so the
+// compiler has no freedom in fusing multiplies and adds and the kernels agree bitwise.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+// a0 v.x + a1 v.y + a2 v.z as one fixed chain
+template <class R> __device__ __forceinline__ R dot3_fixed(R a0, R a1, R a2, V3<R> v) {
+  return fma_rn(a2, v.z, fma_rn(a1, v.y, mul_rn(a0, v.x)));
+}
+// y = B v and y += B v for a row-major 3x3 block B
+template <class R> __device__ __forceinline__ V3<R> block_mul(const R (&b)[9], V3<R> v) {
+  return {dot3_fixed(b[0], b[1], b[2], v), dot3_fixed(b[3], b[4], b[5], v), dot3_fixed(b[6], b[7], b[8], v)};
+}
+template <class R> __device__ __forceinline__ void block_acc(V3<R>& y, const R (&b)[9], V3<R> v) {
+  y.x = add_rn(y.x, dot3_fixed(b[0], b[1], b[2], v));
+  y.y = add_rn(y.y, dot3_fixed(b[3], b[4], b[5], v));
+  y.z = add_rn(y.z, dot3_fixed(b[6], b[7], b[8], v));
+}
+
 // CG direction vectors are the gathered operand of the SpMV: in FP32 they are stored as
 // 16-byte float4 (x, y, z, 0) so a neighbour gather is one aligned load.
 template <class R> struct PStride { static constexpr int v = 3; };
@@ -118,10 +140,6 @@ template <class R> __device__ __forceinline__ V3<R> axpy3(R s, V3<R> x, V3<R> y)
 template <class R> __device__ __forceinline__ double ddot3(V3<R> a, V3<R> b) {
   return (double)a.x * (double)b.x + (double)a.y * (double)b.y + (double)a.z * (double)b.z;
 }
-// Per-row dot product in the batch precision; the sums over rows are FP64.
-template <class R> __device__ __forceinline__ double rdot3(V3<R> a, V3<R> b) {
-  return (double)(a.x * b.x + a.y * b.y + a.z * b.z);
-}
 
 // CG dot-product accumulator of one thread: FP64 in FP64 mode; in FP32 mode a
 // float-float, so the in-warp sum runs on the FP32 pipe at FP64-like accuracy.  Each
@@ -132,9 +150,11 @@ template <class R> using acc_t = typename CGAcc<R>::T;
 
 template <class R> __device__ __forceinline__ acc_t<R> acc_zero() { return 0.0; }
 template <> __device__ __forceinline__ FF acc_zero<float>() { return {0.f, 0.f}; }
-template <class R> __device__ __forceinline__ acc_t<R> acc_dot3(V3<R> a, V3<R> b) { return rdot3(a, b); }
+template <class R> __device__ __forceinline__ acc_t<R> acc_dot3(V3<R> a, V3<R> b) {
+  return (double)dot3_fixed(a.x, a.y, a.z, b);
+}
 template <> __device__ __forceinline__ FF acc_dot3<float>(V3<float> a, V3<float> b) {
-  return {a.x * b.x + a.y * b.y + a.z * b.z, 0.f};
+  return {dot3_fixed(a.x, a.y, a.z, b), 0.f};
 }
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
@@ -155,9 +175,8 @@ __device__ __forceinline__ float alpha_cast(FF a) { return a.hi; }  // = (float)
 template <class R>
 __device__ __forceinline__ V3<R> apply_dinv(const R* __restrict__ D, int Np, int i, V3<R> r) {
   const size_t n = (size_t)Np;
-  return {D[i] * r.x + D[n + i] * r.y + D[2 * n + i] * r.z,
-          D[3 * n + i] * r.x + D[4 * n + i] * r.y + D[5 * n + i] * r.z,
-          D[6 * n + i] * r.x + D[7 * n + i] * r.y + D[8 * n + i] * r.z};
+  return {dot3_fixed(D[i], D[n + i], D[2 * n + i], r), dot3_fixed(D[3 * n + i], D[4 * n + i], D[5 * n + i], r),
+          dot3_fixed(D[6 * n + i], D[7 * n + i], D[8 * n + i], r)};
 }
 
 // Block sum of NV doubles (blockDim.x == kThreads); result valid in thread 0.
@@ -605,7 +624,7 @@ __global__ void k_cond_set(Dev<R> d, cudaGraphConditionalHandle cond) {
 // so bitwise the values k_cg_dir would write) or reads what k_cg_dir wrote.
 template <class R>
 __device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
-  return {fma(beta, pold.x, z.x), fma(beta, pold.y, z.y), fma(beta, pold.z, z.z)};
+  return {fma_rn(beta, pold.x, z.x), fma_rn(beta, pold.y, z.y), fma_rn(beta, pold.z, z.z)};
 }
 
 // partial of warp `wp` (0..7) of work entry w: index w * 8 + wp
@@ -692,9 +711,10 @@ __device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, con
     pi = ldp(pnew, i);
   }
   const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
-  V3<R> y = {lds(a0) * pi.x + lds(a0 + 32) * pi.y + lds(a0 + 64) * pi.z,
-             lds(a0 + 96) * pi.x + lds(a0 + 128) * pi.y + lds(a0 + 160) * pi.z,
-             lds(a0 + 192) * pi.x + lds(a0 + 224) * pi.y + lds(a0 + 256) * pi.z};
+  R ab[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) ab[t] = lds(a0 + 32 * t);
+  V3<R> y = block_mul(ab, pi);
   int q = 1;
   for (; q + 1 < K; q += 2) {  // two slots per iteration: more loads in flight
     const int e0 = (base + q) * 32 + lane, e1 = e0 + 32;
@@ -709,24 +729,18 @@ __device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, con
     }
     const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
     const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ldp(pold, j1)) : ldp(pnew, j1);
-    const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
-    const V3<R> d1 = {p1.x - pi.x, p1.y - pi.y, p1.z - pi.z};
-    y.x += av[0] * d0.x + av[1] * d0.y + av[2] * d0.z;
-    y.y += av[3] * d0.x + av[4] * d0.y + av[5] * d0.z;
-    y.z += av[6] * d0.x + av[7] * d0.y + av[8] * d0.z;
-    y.x += bv[0] * d1.x + bv[1] * d1.y + bv[2] * d1.z;
-    y.y += bv[3] * d1.x + bv[4] * d1.y + bv[5] * d1.z;
-    y.z += bv[6] * d1.x + bv[7] * d1.y + bv[8] * d1.z;
+    block_acc(y, av, V3<R>{p0.x - pi.x, p0.y - pi.y, p0.z - pi.z});
+    block_acc(y, bv, V3<R>{p1.x - pi.x, p1.y - pi.y, p1.z - pi.z});
   }
   if (q < K) {
     const int e0 = (base + q) * 32 + lane;
     const int j0 = lds(d.cols + e0);
     const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
+    R av[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) av[t] = lds(a + 32 * t);
     const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
-    const V3<R> d0 = {p0.x - pi.x, p0.y - pi.y, p0.z - pi.z};
-    y.x += lds(a) * d0.x + lds(a + 32) * d0.y + lds(a + 64) * d0.z;
-    y.y += lds(a + 96) * d0.x + lds(a + 128) * d0.y + lds(a + 160) * d0.z;
-    y.z += lds(a + 192) * d0.x + lds(a + 224) * d0.y + lds(a + 256) * d0.z;
+    block_acc(y, av, V3<R>{p0.x - pi.x, p0.y - pi.y, p0.z - pi.z});
   }
   st3(d.Ap, i, y);
   return acc_dot3(pi, y);
@@ -749,10 +763,10 @@ __device__ __forceinline__ void update_row(const Dev<R>& d, int i, acc_t<R> al, 
     st3(d.dvl, i, V3<float>{a.lo, b.lo, c.lo});
   } else {
     V3<double> x = ld3(d.dv, i);
-    x = {x.x + al * (double)p.x, x.y + al * (double)p.y, x.z + al * (double)p.z};
+    x = {fma_rn(al, (double)p.x, x.x), fma_rn(al, (double)p.y, x.y), fma_rn(al, (double)p.z, x.z)};
     st3(d.dv, i, x);
   }
-  r = axpy3(-alpha, Ap, r);
+  r = {fma_rn(-alpha, Ap.x, r.x), fma_rn(-alpha, Ap.y, r.y), fma_rn(-alpha, Ap.z, r.z)};
   st3(d.r, i, r);
   const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
   st3(d.z, i, z);
@@ -874,66 +888,172 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
   }
 }
 
-// ------------------------------------------------------------------ cluster tail solver
-// When only a few sheets are still iterating, the device loop above pays a full set of
-// launches per iteration for little work.  The tail solver gives each remaining sheet
-// one thread-block cluster of kTailCluster CTAs that runs the rest of its CG without
-// returning: the same row kernels and the same per-warp partial sums as the loop, with
-// the two reductions of an iteration separated by hardware cluster barriers
-// (release/acquire at cluster scope), so its results are bitwise those of the loop.
-// Every CTA of a cluster derives alpha, beta and the stopping test from the same
-// partials, so all take the same branches; the loop ends at convergence, on a bad
-// scalar or at max_iter.
-constexpr int kTailCluster = 8;
-
-template <class R>
-__global__ void k_tail_prep(Dev<R> d) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    int n = 0;
-    for (int s = 0; s < d.S; ++s)
-      if (!d.cg[s].done) d.tail_list[n++] = s;
-    d.tail_list[d.S] = n;
-  }
-}
+// ------------------------------------------------------------------ per-sheet cluster solver
+// Each sheet is solved to the end by one thread-block cluster of CL CTAs (CL = 1, 2, 4 or 8,
+// by the sheet's size) holding EPC work entries (256 rows each) per CTA, one row per
+// thread.  The row's CG state (r, z, its own direction, the solution) and its column
+// indices stay in registers for the whole solve, so an iteration reads from memory only
+// the matrix row and the neighbours' z and p_{k-1} (L2-resident while the sheet runs).
+// The per-warp partial sums go through shared memory (distributed shared memory across
+// the cluster) and the two reductions of an iteration are separated by CTA or cluster
+// barriers (hardware barriers, release/acquire at cluster scope).  Sheets are independent,
+// so a launch may hold more clusters than fit on the GPU at once: they run as others end.
+// Every CTA forms alpha, beta and the stopping test from the same partial sums in the same
+// order, so all take the same branches.  The arithmetic and the summation orders are those
+// of the device loop above, so the results are bitwise the same.
+constexpr int kColCache = 16;  // column indices kept in registers per row (further slots are loaded)
 
 template <class R> __device__ __forceinline__ acc_t<R> acc_from_double(double x) { return x; }
 template <> __device__ __forceinline__ FF acc_from_double<float>(double x) { return ff_from_double(x); }
 
-template <class R>
-__global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads) k_cg_tail(Dev<R> d, int phase) {
+// CG solution of one row in registers: FP64, or float-float in FP32 mode
+template <class R> struct DvReg {
+  V3<double> x;
+  __device__ __forceinline__ void load(const Dev<R>& d, int i) { x = ld3(d.dv, i); }
+  __device__ __forceinline__ void axpy(double al, V3<R> p) {
+    x = {fma_rn(al, (double)p.x, x.x), fma_rn(al, (double)p.y, x.y), fma_rn(al, (double)p.z, x.z)};
+  }
+  __device__ __forceinline__ void store(const Dev<R>& d, int i) const { st3(d.dv, i, x); }
+};
+template <> struct DvReg<float> {
+  FF a, b, c;
+  __device__ __forceinline__ void load(const Dev<float>& d, int i) {
+    const V3<float> h = ld3(d.dvh, i), l = ld3(d.dvl, i);
+    a = {h.x, l.x};
+    b = {h.y, l.y};
+    c = {h.z, l.z};
+  }
+  __device__ __forceinline__ void axpy(FF al, V3<float> p) {
+    a = ff_add(a, ff_mul(al, p.x));
+    b = ff_add(b, ff_mul(al, p.y));
+    c = ff_add(c, ff_mul(al, p.z));
+  }
+  __device__ __forceinline__ void store(const Dev<float>& d, int i) const {
+    st3(d.dvh, i, V3<float>{a.hi, b.hi, c.hi});
+    st3(d.dvl, i, V3<float>{a.lo, b.lo, c.lo});
+  }
+};
+
+// values written by other CTAs of the cluster in the previous phase: read through L2
+template <class R> __device__ __forceinline__ V3<R> ld3_l2(const R* a, int i) {
+  return {__ldcg(a + 3 * (size_t)i), __ldcg(a + 3 * (size_t)i + 1), __ldcg(a + 3 * (size_t)i + 2)};
+}
+template <class R> __device__ __forceinline__ V3<R> ldp_l2(const R* a, int i) { return ld3_l2(a, i); }
+template <> __device__ __forceinline__ V3<float> ldp_l2<float>(const float* a, int i) {
+  const float4 q = __ldcg(reinterpret_cast<const float4*>(a) + i);
+  return {q.x, q.y, q.z};
+}
+
+template <class R, int EPC>
+__global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(Dev<R> d, const int* __restrict__ sheets, int nsheets,
+                                                             int CL, int phase) {
   namespace cgrp = cooperative_groups;
-  cgrp::cluster_group cl = cgrp::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const int cid = blockIdx.x / kTailCluster;
-  if (cid >= d.tail_list[d.S]) return;  // uniform over the cluster
-  const int s = d.tail_list[cid];
-  // Thread 0 of each CTA forms the iteration's scalars (FP64) from the partial sums and
-  // hands the rest of the CTA only what the row kernels take, so no other thread does
-  // FP64 arithmetic.
+  const int cid = blockIdx.x / CL;
+  const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
+  if (cid >= nsheets) return;               // uniform over the cluster
+  const int s = sheets[cid];
+  if (d.cg[s].done) return;  // uniform: written only at the end of this sheet's solve
+
+  // partial sums of the CTA's warps: [0] p.Ap, [1] r.z, [2] r.r, per local entry and warp
+  __shared__ double sp[3][EPC][kWarpsPerEntry];
   __shared__ acc_t<R> bc_alpha;
   __shared__ R bc_beta;
   __shared__ int bc_stop;
-  const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
+
+  const int jl = threadIdx.x / kThreads, t = threadIdx.x - jl * kThreads;
+  const int lane = threadIdx.x & 31, wp = t >> 5;
   const int w0 = d.sheet_wfirst[s], w1 = d.sheet_wfirst[s + 1];
+  const int w = w0 + rank + CL * jl;
+  const bool on = w < w1 && t < d.work_rows[w];
+  const int i = on ? d.work_row0[w] + t : 0;
+
+  auto barrier = [&]() {
+    if (CL > 1) cgrp::this_cluster().sync();
+    else __syncthreads();
+  };
+  // the sheet's sum of one partial array, in the order of sheet_sum (lane-strided, then a
+  // shuffle tree); called by one full warp
+  auto sheet_total = [&](int which) {
+    double acc = 0.0;
+    for (int q = w0 * kWarpsPerEntry + lane; q < w1 * kWarpsPerEntry; q += 32) {
+      const int e = q / kWarpsPerEntry - w0, pw = q % kWarpsPerEntry;
+      const int rk = e % CL, jj = e / CL;
+      const double* src = &sp[which][jj][pw];
+      if (CL > 1) src = cgrp::this_cluster().map_shared_rank(src, rk);
+      acc += *src;
+    }
+    return warp_sum(acc);
+  };
+
+  // row state
   int k = d.cg[s].iters;
   R beta_r = (R)d.cg[s].beta;
-  // thread 0's copy of the sheet's CG state
+  V3<R> r = {R(0), R(0), R(0)}, z = r, pold = r, Ap = r;
+  DvReg<R> x;
+  int K = 0, base = 0, col[kColCache];
+  const int sl_lane = i & 31;
+  if (on) {
+    r = ld3(d.r, i);
+    z = ld3(d.z, i);
+    pold = ldp(pbuf(d, k + 1), i);
+    x.load(d, i);
+    const int sl = i >> 5;
+    K = d.slice_K[sl];
+    base = d.slice_base[sl];
+  }
+#pragma unroll
+  for (int q = 0; q < kColCache; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
+  // thread 0's copy of the sheet's scalars
   double rz = d.cg[s].rz, beta = d.cg[s].beta, rr = d.cg[s].rr, pAp = 0.0, al = 0.0;
   const double bb = d.cg[s].bb;
   int status = 0;
+
   while (true) {
-    for (int w = w0 + rank; w < w1; w += kTailCluster) {
-      acc_t<R> v = acc_zero<R>();
-      if (threadIdx.x < d.work_rows[w])
-        v = spmv_row<R, true>(d, d.work_row0[w] + threadIdx.x, beta_r, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
-      const double t = acc_warp_total(v);
-      if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = t;
+    // ---- Ap = A p_k, p_k = z_k + beta_k p_{k-1} formed on the fly (own row and neighbours)
+    acc_t<R> vpart = acc_zero<R>();
+    V3<R> pi = {R(0), R(0), R(0)};
+    if (on) {
+      const R* __restrict__ pprev = pbuf(d, k + 1);
+      pi = next_dir(z, beta_r, pold);
+      stp(const_cast<R*>(pbuf(d, k)), i, pi);
+      const R* a0 = d.Aval + (size_t)base * 32 * 9 + sl_lane;
+      R ab[9];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) ab[m] = __ldcg(a0 + 32 * m);
+      V3<R> y = block_mul(ab, pi);
+#pragma unroll
+      for (int q = 1; q <= kColCache; ++q) {
+        if (q < K) {
+          const int j = col[q - 1];
+          const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
+          R av[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) av[m] = __ldcg(a + 32 * m);
+          const V3<R> pj = next_dir(ld3_l2(d.z, j), beta_r, ldp_l2(pprev, j));
+          block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
+        }
+      }
+      for (int q = kColCache + 1; q < K; ++q) {
+        const int j = d.cols[(base + q) * 32 + sl_lane];
+        const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
+        R av[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) av[m] = __ldcg(a + 32 * m);
+        const V3<R> pj = next_dir(ld3_l2(d.z, j), beta_r, ldp_l2(pprev, j));
+        block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
+      }
+      Ap = y;
+      vpart = acc_dot3(pi, y);
     }
-    cl.sync();
+    {
+      const double tw = acc_warp_total(vpart);
+      if (lane == 0) sp[0][jl][wp] = tw;
+    }
+    barrier();
     if (threadIdx.x < 32) {
-      const double t = sheet_sum(d, d.part_c, s);
+      const double tsum = sheet_total(0);
       if (threadIdx.x == 0) {
-        pAp = t;
+        pAp = tsum;
         int stop = 0;
         if (!isfinite(pAp)) {
           status |= CLOTH_STATUS_NONFINITE;
@@ -950,20 +1070,30 @@ __global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads)
     }
     __syncthreads();
     if (bc_stop) break;
-    const acc_t<R> alpha = bc_alpha;
-    for (int w = w0 + rank; w < w1; w += kTailCluster) {
-      acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>();
-      if (threadIdx.x < d.work_rows[w]) update_row(d, d.work_row0[w] + threadIdx.x, alpha, pbuf(d, k), v0, v1);
-      const double t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
-      if (lane_w == 0) {
-        d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
-        d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
+    // ---- dv += alpha p_k, r -= alpha Ap, z = D^{-1} r
+    acc_t<R> va = acc_zero<R>(), vb = acc_zero<R>();
+    if (on) {
+      const acc_t<R> alpha = bc_alpha;
+      x.axpy(alpha, pi);
+      const R am = -alpha_cast(alpha);
+      r = {fma_rn(am, Ap.x, r.x), fma_rn(am, Ap.y, r.y), fma_rn(am, Ap.z, r.z)};
+      z = apply_dinv(d.dinv, d.Np, i, r);
+      st3(d.z, i, z);  // gathered by the neighbours in the next iteration
+      va = acc_dot3(r, z);
+      vb = acc_dot3(r, r);
+      pold = pi;
+    }
+    {
+      const double ta = acc_warp_total(va), tb = acc_warp_total(vb);
+      if (lane == 0) {
+        sp[1][jl][wp] = ta;
+        sp[2][jl][wp] = tb;
       }
     }
-    cl.sync();
+    barrier();
     k += 1;
     if (threadIdx.x < 32) {
-      const double a = sheet_sum(d, d.part_a, s), b = sheet_sum(d, d.part_b, s);
+      const double a = sheet_total(1), b = sheet_total(2);
       if (threadIdx.x == 0) {
         rr = b;
         beta = a / rz;
@@ -986,6 +1116,13 @@ __global__ void __cluster_dims__(kTailCluster, 1, 1) __launch_bounds__(kThreads)
     if (bc_stop) break;
     beta_r = bc_beta;
   }
+  if (on) {
+    x.store(d, i);
+    st3(d.r, i, r);
+    st3(d.Ap, i, Ap);
+  }
+  // no CTA leaves while another may still read its shared memory
+  if (CL > 1) cgrp::this_cluster().sync();
   if (rank == 0 && threadIdx.x == 0) {
     CGSheet& c = d.cg[s];
     c.iters = k;

@@ -33,6 +33,13 @@ namespace cloth {
 
 template <class R>
 class Engine final : public EngineBase {
+  // a size class of the per-sheet cluster solver: CL CTAs per cluster, EPC work entries per CTA
+  struct SheetClass {
+    int CL = 1, EPC = 1, offset = 0, n = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+
   // Every host-issued kernel launch goes through here so the launch count of a call
   // is known (CG loop-body kernels are counted on the device instead).
   template <class... P, class... A>
@@ -52,6 +59,11 @@ class Engine final : public EngineBase {
     if (host_active_) cudaFreeHost(host_active_);
     if (ev0_) cudaEventDestroy(ev0_);
     if (ev1_) cudaEventDestroy(ev1_);
+    if (fork_ev_) cudaEventDestroy(fork_ev_);
+    for (auto& c : classes_) {
+      if (c.stream) cudaStreamDestroy(c.stream);
+      if (c.done) cudaEventDestroy(c.done);
+    }
     for (void* p : allocs_) cudaFree(p);
   }
 
@@ -140,7 +152,6 @@ class Engine final : public EngineBase {
     d.part_a = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.part_b = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.part_c = alloc<double>((size_t)d.NW * kWarpsPerEntry, &rc);
-    d.tail_list = alloc<int>((size_t)L_.S + 1, &rc);
     d.active = alloc<int>(1, &rc);
     d.iter_total = alloc<unsigned long long>(3, &rc);
     d.body_runs = alloc<unsigned long long>(3, &rc);
@@ -190,26 +201,54 @@ class Engine final : public EngineBase {
     }
     cg_grid_ = std::max(1, std::min(d.NW, sms * std::max(1, std::min(per_sm, per_sm2))));
     resident_grid_ = cg_grid_;
-    // tail solver: as many sheets as clusters can be resident at once, and only when every
-    // sheet is small enough for one cluster (<= 64 work entries = 16384 rows)
+    // per-sheet cluster solver: every sheet of at most 8 x 4 work entries (8192 rows) gets a
+    // cluster of CL CTAs with EPC entries each, CL * EPC >= its entries; sheets of a class
+    // (CL, EPC) are listed largest first, so the longest solves start first
     {
-      cudaLaunchConfig_t lc = {};
-      lc.gridDim = dim3(kTailCluster);
-      lc.blockDim = dim3(kThreads);
-      cudaLaunchAttribute at;
-      at.id = cudaLaunchAttributeClusterDimension;
-      at.val.clusterDim.x = kTailCluster;
-      at.val.clusterDim.y = 1;
-      at.val.clusterDim.z = 1;
-      lc.attrs = &at;
-      lc.numAttrs = 1;
-      int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, k_cg_tail<R>, &lc) != cudaSuccess) clusters = 0;
       int max_entries = 0;
       for (int s2 = 0; s2 < L_.S; ++s2) max_entries = std::max(max_entries, L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2]);
-      tail_clusters_ = (max_entries <= 64) ? std::max(0, std::min(L_.S, clusters)) : 0;
+      sheet_solver_ok_ = max_entries <= 32;
+      if (sheet_solver_ok_) {
+        std::map<std::pair<int, int>, std::vector<int>> cls;
+        for (int s2 = 0; s2 < L_.S; ++s2) {
+          const int E = L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2];
+          int CL = 1, EPC = 1;
+          if (E <= 1) CL = 1, EPC = 1;
+          else if (E <= 2) CL = 1, EPC = 2;
+          else if (E <= 4) CL = 2, EPC = 2;
+          else if (E <= 8) CL = 4, EPC = 2;
+          else if (E <= 16) CL = 8, EPC = 2;
+          else CL = 8, EPC = 4;
+          cls[{CL, EPC}].push_back(s2);
+        }
+        std::vector<int> lists;
+        for (auto& kv : cls) {
+          auto& v = kv.second;
+          std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+            return L_.sheet_wfirst[a + 1] - L_.sheet_wfirst[a] > L_.sheet_wfirst[b + 1] - L_.sheet_wfirst[b];
+          });
+          SheetClass c;
+          c.CL = kv.first.first;
+          c.EPC = kv.first.second;
+          c.offset = (int)lists.size();
+          c.n = (int)v.size();
+          lists.insert(lists.end(), v.begin(), v.end());
+          if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess ||
+              cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
+            *err = "CUDA stream setup failed";
+            return CLOTH_ERR_CUDA;
+          }
+          classes_.push_back(c);
+        }
+        sheet_lists_ = upload(lists, &rc);
+        if (rc != CLOTH_OK || cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
+          *err = "CUDA setup failed";
+          return rc != CLOTH_OK ? rc : CLOTH_ERR_CUDA;
+        }
+      }
       cudaGetLastError();
     }
+    if (o_.cg_handover > 0) handover_ = o_.cg_handover;
     if (o_.cg_schedule >= 0) {
       set_schedule(o_.cg_schedule);
     } else {
@@ -537,7 +576,9 @@ class Engine final : public EngineBase {
     schedule_ = sched & 7;
     sched_fused_ = (schedule_ & 2) != 0;
     cg_grid_ = (schedule_ & 1) ? resident_grid_ : d_.NW;
-    d_.tail_threshold = (schedule_ & 4) ? tail_clusters_ : 0;
+    // bit 2: every sheet is solved by the per-sheet cluster solver (the device loop
+    // hands over at once)
+    d_.tail_threshold = ((schedule_ & 4) && sheet_solver_ok_) ? std::min(L_.S, handover_) : 0;
   }
 
   int scalar_grid() const { return (L_.S * 32 + 255) / 256; }
@@ -606,12 +647,14 @@ class Engine final : public EngineBase {
     }
     std::ostringstream key;
     key << prop.name << "|" << (sizeof(R) == 4 ? "f32" : "f64") << "|rows=" << L_.Np << "|entries=" << d_.NW
-        << "|slots=" << L_.total_slots();
+        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover;
     const std::string path = tune_cache_path();
     auto cache = path.empty() ? std::map<std::string, int>() : read_tune_cache(path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-      set_schedule((it->second & 3) | (tail_clusters_ > 0 ? 4 : 0));
+      // value: schedule (bits 0-2) + 8 x hand-over point
+      if (o_.cg_handover == 0 && (it->second >> 3) > 0) handover_ = it->second >> 3;
+      set_schedule(it->second & 7);
       return CLOTH_OK;
     }
     cudaStream_t st = cap_stream_;
@@ -632,7 +675,7 @@ class Engine final : public EngineBase {
     int best_s = 3;
     const int iters = 12;
     for (int sched = 0; sched < 4; ++sched) {
-      set_schedule(sched);  // loop kernels only (bit 2, the tail solver, is set by eligibility)
+      set_schedule(sched);  // loop kernels only (bit 2, the per-sheet solver, is set by eligibility)
       k_solve_begin<R><<<1, 32, 0, st>>>(d_);
       k_cg_init<R><<<cg_grid_, kThreads, 0, st>>>(d_, d_.bvec);
       k_cg_scalar_init<R><<<scalar_grid(), 256, 0, st>>>(d_, kPhaseForward);
@@ -648,15 +691,73 @@ class Engine final : public EngineBase {
         best_s = sched;
       }
     }
-    if (tail_clusters_ > 0) best_s |= 4;
+    // then whole solves of this system: the loop alone, and the loop handing over to the
+    // per-sheet cluster solver at several points (unless the caller fixed the point)
+    if (sheet_solver_ok_) {
+      std::vector<int> points;
+      if (o_.cg_handover > 0) {
+        points.push_back(handover_);
+      } else {
+        for (int f : {16, 8, 4, 2, 1}) {
+          const int p = std::max(1, L_.S / f);
+          if (points.empty() || points.back() != p) points.push_back(p);
+        }
+      }
+      set_schedule(best_s);
+      float t_best = 0.f;
+      CLOTH_TRY(time_solve(&t_best));
+      int best_h = 0;
+      for (int p : points) {
+        handover_ = p;
+        set_schedule(best_s | 4);
+        float t = 0.f;
+        CLOTH_TRY(time_solve(&t));
+        if (t < t_best) {
+          t_best = t;
+          best_h = p;
+        }
+      }
+      if (best_h > 0) {
+        handover_ = best_h;
+        best_s |= 4;
+      }
+    }
     set_schedule(best_s);
     d_.material = mat_;
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
     CLOTH_CUDA(cudaStreamSynchronize(st));
     if (!path.empty()) {
-      cache[key.str()] = best_s;
+      cache[key.str()] = best_s | ((best_s & 4) ? handover_ << 3 : 0);
       write_tune_cache(path, cache);
     }
+    return CLOTH_OK;
+  }
+
+  // Device time [ms] of one solve of the assembled system, captured as it runs in a call
+  // (autotuner): one untimed replay, then one timed.
+  int time_solve(float* ms) {
+    cudaStream_t st = cap_stream_;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CLOTH_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    const int rc = solve(d_.bvec, kPhaseForward, st, true);
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != CLOTH_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc != CLOTH_OK) return rc;
+      CLOTH_CUDA(ec);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CLOTH_CUDA(ei);
+    cudaError_t e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0_, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1_, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1_);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ev0_, ev1_);
+    cudaGraphExecDestroy(ge);
+    CLOTH_CUDA(e);
     return CLOTH_OK;
   }
 
@@ -691,7 +792,7 @@ class Engine final : public EngineBase {
       cudaGraph_t out = nullptr;
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
-      emit_tail(st, phase);
+      CLOTH_TRY(emit_tail(st, phase));
       emit_solution(st);
       return CLOTH_OK;
     }
@@ -707,7 +808,7 @@ class Engine final : public EngineBase {
       launched += poll;
       CLOTH_CUDA(cudaGetLastError());
     }
-    emit_tail(st, phase);
+    CLOTH_TRY(emit_tail(st, phase));
     emit_solution(st);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
@@ -718,11 +819,36 @@ class Engine final : public EngineBase {
     if constexpr (std::is_same<R, float>::value) launch(k_cg_solution<R>, dim3(grid_rows()), dim3(256), st, d_);
   }
 
-  // the sheets still running after the device loop finish in the cluster tail solver
-  void emit_tail(cudaStream_t st, int phase) {
-    if (d_.tail_threshold <= 0) return;
-    launch(k_tail_prep<R>, dim3(1), dim3(32), st, d_);
-    launch(k_cg_tail<R>, dim3(kTailCluster * d_.tail_threshold), dim3(kThreads), st, d_, phase);
+  // the sheets still running after the device loop finish in the per-sheet cluster
+  // solver: one launch per size class, on its own stream so the classes run side by side
+  template <int EPC>
+  cudaError_t launch_class(const SheetClass& c, int phase) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(c.n * c.CL));
+    lc.blockDim = dim3(kThreads * EPC);
+    lc.stream = c.stream;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)c.CL;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    lc.attrs = &at;
+    lc.numAttrs = c.CL > 1 ? 1 : 0;
+    ++launches_;
+    return cudaLaunchKernelEx(&lc, k_cg_sheet<R, EPC>, d_, (const int*)(sheet_lists_ + c.offset), c.n, c.CL, phase);
+  }
+
+  int emit_tail(cudaStream_t st, int phase) {
+    if (d_.tail_threshold <= 0) return CLOTH_OK;
+    CLOTH_CUDA(cudaEventRecord(fork_ev_, st));
+    for (auto& c : classes_) {
+      CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
+      CLOTH_CUDA(c.EPC == 1 ? launch_class<1>(c, phase) : c.EPC == 2 ? launch_class<2>(c, phase)
+                                                                      : launch_class<4>(c, phase));
+      CLOTH_CUDA(cudaEventRecord(c.done, c.stream));
+      CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
+    }
+    return CLOTH_OK;
   }
 
   // One implicit step from (x, v) to (xn, vn); F: user-layout force row or null.
@@ -873,7 +999,11 @@ class Engine final : public EngineBase {
   std::vector<CachedGraph> graphs_;
   int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
   int cg_grid_ = 1;       // CTAs of the CG kernels (the schedule's choice)
-  int tail_clusters_ = 0; // sheets the cluster tail solver can take (0: not eligible)
+  std::vector<SheetClass> classes_;  // size classes of the per-sheet cluster solver
+  const int* sheet_lists_ = nullptr;  // their sheets, class after class
+  bool sheet_solver_ok_ = false;      // every sheet fits one cluster
+  int handover_ = 1 << 30;            // sheets left when the device loop hands over
+  cudaEvent_t fork_ev_ = nullptr;
   int resident_grid_ = 1; // CTAs resident at once on the whole GPU
   bool sched_fused_ = true;
   int schedule_ = 3;

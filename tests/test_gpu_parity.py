@@ -296,7 +296,7 @@ def test_batched_sheets_match_their_own_oracles(oracle_mod):
 def test_checkpointing_and_exec_modes_agree(oracle_mod):
     """Checkpoint-and-recompute (C = 3 of 10 steps), the plain host-polled CG and the CG
     kernel schedules (fused or separate direction update, resident or per-entry grid,
-    with or without the cluster tail solver, and the autotuned one) give bitwise the same
+    with or without the per-sheet cluster solver, and the autotuned one) give bitwise the same
     trajectory and gradients as the captured-graph run without checkpoints."""
     sheets = sheets_mixed(seed=21)[:2]
     steps, dt = 10, 1 / 30
@@ -318,6 +318,39 @@ def test_checkpointing_and_exec_modes_agree(oracle_mod):
         np.testing.assert_array_equal(r[2], res[0][2])
     for r in res:
         np.testing.assert_array_equal(r[3], r[1])
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_sheet_solver_matches_device_loop_bitwise(precision):
+    """The per-sheet cluster solver (schedule bit 2) against the device loop alone, on
+    sheets of 1 to 20 work entries (every cluster size and entries-per-CTA class): bitwise
+    the same trajectory, gradients and per-sheet iteration counts, in graph and plain
+    execution."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    sheets = []
+    for N in (16, 20, 30, 40, 50, 64, 70):
+        rest, tris = W.grid_mesh(N)
+        sheets.append(W.Sheet(N, rest, tris, W.pins(N, "top2"), W.sample_material(rng), None))
+    dtype = torch.float32 if precision == "f32" else torch.float64
+    res = []
+    for exec_mode, sched in (("graph", 2), ("graph", 6), ("plain", 7)):
+        b = make_batch(sheets, steps=4, dt=1 / 30, precision=precision, tol=1e-7, exec_mode=exec_mode, schedule=sched)
+        assert b.matrix_info()["cg_schedule"] == sched
+        x0 = to_cuda(np.concatenate([s.rest for s in sheets]), dtype)
+        mat = to_cuda(_materials(sheets), dtype)
+        traj, st = b.forward(mat, x0, torch.zeros_like(x0), None)
+        g = b.backward(torch.ones_like(traj))
+        torch.cuda.synchronize()
+        assert int(st.max()) == 0 and int(g["status"].max()) == 0
+        it = [b.sheet_iterations(ph) for ph in ("forward", "adjoint")]
+        res.append((to_np(traj), to_np(g["material"]), to_np(g["x0"]), it))
+    for r in res[1:]:
+        np.testing.assert_array_equal(r[0], res[0][0])
+        np.testing.assert_array_equal(r[1], res[0][1])
+        np.testing.assert_array_equal(r[2], res[0][2])
+        for (m1, t1), (m0, t0) in zip(r[3], res[0][3]):
+            np.testing.assert_array_equal(m1, m0)
+            np.testing.assert_array_equal(t1, t0)
 
 
 def test_cg_maxiter_status_and_free_fall():
