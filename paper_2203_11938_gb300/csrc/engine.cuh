@@ -35,6 +35,7 @@ constexpr int kElemThreads = 128;
 
 struct CGSheet {
   double rz, rr, bb, pAp, alpha, beta;
+  double stop_rr;            // (tol |b|)^2: the solve ends when r.r <= stop_rr
   float alpha_hi, alpha_lo;  // alpha as a float-float (FP32 mode's solution update)
   int iters, done, status, pad;
 };
@@ -684,6 +685,7 @@ __global__ void k_cg_scalar_init(Dev<R> d, int phase) {
   c.rz = rz;
   c.rr = rr;
   c.bb = rr;
+  c.stop_rr = d.tol * d.tol * rr;
   c.beta = 0.0;
   c.iters = 0;
   c.done = 0;
@@ -691,7 +693,7 @@ __global__ void k_cg_scalar_init(Dev<R> d, int phase) {
   if (!isfinite(rr)) {
     c.status |= CLOTH_STATUS_NONFINITE;
     fin = true;
-  } else if (rr == 0.0 || sqrt(rr) <= d.tol * sqrt(rr)) {
+  } else if (rr == 0.0 || rr <= c.stop_rr) {
     fin = true;
   }
   if (fin) finish_sheet(d, s, phase, 0, 0);
@@ -864,7 +866,7 @@ __global__ void k_cg_scalar_beta(Dev<R> d, int phase, cudaGraphConditionalHandle
   if (!isfinite(rr) || !isfinite(rz)) {
     c.status |= CLOTH_STATUS_NONFINITE;
     finish_sheet(d, s, phase, cond, use_cond);
-  } else if (sqrt(rr) <= d.tol * sqrt(c.bb)) {
+  } else if (rr <= c.stop_rr) {
     finish_sheet(d, s, phase, cond, use_cond);
   } else if (c.iters >= d.maxit) {
     c.status |= CLOTH_STATUS_CG_MAXITER;
@@ -934,7 +936,9 @@ template <> struct DvReg<float> {
   }
 };
 
-// values written by other CTAs of the cluster in the previous phase: read through L2
+// The matrix, its column indices and the block-Jacobi inverse do not change during a
+// solve and are read through the read-only (L1) path; values written by other threads
+// in the previous phase (z, p) are read through L2.
 template <class R> __device__ __forceinline__ V3<R> ld3_l2(const R* a, int i) {
   return {__ldcg(a + 3 * (size_t)i), __ldcg(a + 3 * (size_t)i + 1), __ldcg(a + 3 * (size_t)i + 2)};
 }
@@ -1005,7 +1009,7 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   for (int q = 0; q < kColCache; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
   // thread 0's copy of the sheet's scalars
   double rz = d.cg[s].rz, beta = d.cg[s].beta, rr = d.cg[s].rr, pAp = 0.0, al = 0.0;
-  const double bb = d.cg[s].bb;
+  const double stop_rr = d.cg[s].stop_rr;
   int status = 0;
 
   while (true) {
@@ -1019,7 +1023,7 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
       const R* a0 = d.Aval + (size_t)base * 32 * 9 + sl_lane;
       R ab[9];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) ab[m] = __ldcg(a0 + 32 * m);
+      for (int m = 0; m < 9; ++m) ab[m] = __ldg(a0 + 32 * m);
       V3<R> y = block_mul(ab, pi);
 #pragma unroll
       for (int q = 1; q <= kColCache; ++q) {
@@ -1028,17 +1032,17 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
           const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
           R av[9];
 #pragma unroll
-          for (int m = 0; m < 9; ++m) av[m] = __ldcg(a + 32 * m);
+          for (int m = 0; m < 9; ++m) av[m] = __ldg(a + 32 * m);
           const V3<R> pj = next_dir(ld3_l2(d.z, j), beta_r, ldp_l2(pprev, j));
           block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
         }
       }
       for (int q = kColCache + 1; q < K; ++q) {
-        const int j = d.cols[(base + q) * 32 + sl_lane];
+        const int j = __ldg(d.cols + (base + q) * 32 + sl_lane);
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
         R av[9];
 #pragma unroll
-        for (int m = 0; m < 9; ++m) av[m] = __ldcg(a + 32 * m);
+        for (int m = 0; m < 9; ++m) av[m] = __ldg(a + 32 * m);
         const V3<R> pj = next_dir(ld3_l2(d.z, j), beta_r, ldp_l2(pprev, j));
         block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
       }
@@ -1077,7 +1081,12 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
       x.axpy(alpha, pi);
       const R am = -alpha_cast(alpha);
       r = {fma_rn(am, Ap.x, r.x), fma_rn(am, Ap.y, r.y), fma_rn(am, Ap.z, r.z)};
-      z = apply_dinv(d.dinv, d.Np, i, r);
+      {
+        R dm[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) dm[m] = __ldg(d.dinv + (size_t)m * d.Np + i);
+        z = block_mul(dm, r);  // = apply_dinv
+      }
       st3(d.z, i, z);  // gathered by the neighbours in the next iteration
       va = acc_dot3(r, z);
       vb = acc_dot3(r, r);
@@ -1102,7 +1111,7 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
         if (!isfinite(rr) || !isfinite(a)) {
           status |= CLOTH_STATUS_NONFINITE;
           stop = 1;
-        } else if (sqrt(rr) <= d.tol * sqrt(bb)) {
+        } else if (rr <= stop_rr) {
           stop = 1;
         } else if (k >= d.maxit) {
           status |= CLOTH_STATUS_CG_MAXITER;

@@ -241,6 +241,11 @@ class Engine final : public EngineBase {
           classes_.push_back(c);
         }
         sheet_lists_ = upload(lists, &rc);
+        // the kernel needs little shared memory: leave the rest of the SM's storage to L1,
+        // which holds the matrix rows it rereads every iteration
+        cudaFuncSetAttribute(k_cg_sheet<R, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
+        cudaFuncSetAttribute(k_cg_sheet<R, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
+        cudaFuncSetAttribute(k_cg_sheet<R, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         if (rc != CLOTH_OK || cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
           *err = "CUDA setup failed";
           return rc != CLOTH_OK ? rc : CLOTH_ERR_CUDA;
