@@ -345,14 +345,15 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (spmv_ms / 1e3) / 1e9
     traffic = committed_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (3x3-block SELL-32 difference-form SpMV, per-sheet FP64 p.Ap)",
+    roofline = {"bound": "hbm", "kernel": "k_cg_spmv (3x3-block SELL-32 difference-form SpMV, per-warp p.Ap partials)",
                 "cg_schedule": mi["cg_schedule"],
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(spmv_ms, 5),
                 "bytes_per_vertex": round(alg_bytes / mi["rows"], 1),
                 "cg_update_ms": round(upd_ms, 5),
-                # update: p, Ap, r, z (3 es each), dv FP64 read+write, r write, 3x3 inverse (9 es)
+                # update: p, Ap, r, z (3 es each), the solution dv read+write (FP64, or float-float
+                # hi + lo in FP32 mode: 24 B each way), r write, 3x3 inverse (9 es)
                 "cg_update_GBps": round(mi["rows"] * (3 * es * 5 + 9 * es + 48) / (upd_ms / 1e3) / 1e9, 1)}
 
     log(f"roofline {roofline}")

@@ -33,12 +33,22 @@ namespace cloth {
 constexpr int kThreads = kRowsPerBlock;  // row kernels: one CTA per work entry
 constexpr int kElemThreads = 128;
 
+// Per-sheet CG scalars.  FP64 mode computes in the doubles; FP32 mode computes r.z,
+// alpha and the stopping threshold as float-float and keeps beta as the float the
+// direction update takes (the doubles then hold the values at the start of the solve).
 struct CGSheet {
   double rz, rr, bb, pAp, alpha, beta;
-  double stop_rr;            // (tol |b|)^2: the solve ends when r.r <= stop_rr
-  float alpha_hi, alpha_lo;  // alpha as a float-float (FP32 mode's solution update)
+  double stop_rr;         // (tol |b|)^2: the solve ends when r.r <= stop_rr
+  FF rz_f, stop_f, alpha_f;
+  float beta_f;
   int iters, done, status, pad;
 };
+
+// CG dot-product accumulator of one thread: FP64 in FP64 mode; in FP32 mode a
+// float-float, so the sums run on the FP32 pipe at near-FP64 accuracy.
+template <class R> struct CGAcc { using T = double; };
+template <> struct CGAcc<float> { using T = FF; };
+template <class R> using acc_t = typename CGAcc<R>::T;
 
 enum Phase { kPhaseForward = 0, kPhaseBackward = 1, kPhaseRecompute = 2 };
 
@@ -70,7 +80,7 @@ struct Dev {
   double* dv;  // CG solution (dv, or lambda in the adjoint): FP64 after each solve
   float *dvh, *dvl;  // FP32 mode: the solution accumulated as float-float hi + lo [Np][3]
   CGSheet* cg;
-  double *part_a, *part_b, *part_c;  // per-warp partial sums [NW * 8] (r.z, r.r, p.Ap)
+  acc_t<R> *part_a, *part_b, *part_c;  // per-warp partial sums [NW * 8] (r.z, r.r, p.Ap)
   int tail_threshold;                 // the device loop hands over when <= this many sheets remain
   int* active;
   unsigned long long* iter_total;
@@ -142,13 +152,6 @@ template <class R> __device__ __forceinline__ double ddot3(V3<R> a, V3<R> b) {
   return (double)a.x * (double)b.x + (double)a.y * (double)b.y + (double)a.z * (double)b.z;
 }
 
-// CG dot-product accumulator of one thread: FP64 in FP64 mode; in FP32 mode a
-// float-float, so the in-warp sum runs on the FP32 pipe at FP64-like accuracy.  Each
-// warp's sum leaves as one double; sums over warps are FP64.
-template <class R> struct CGAcc { using T = double; };
-template <> struct CGAcc<float> { using T = FF; };
-template <class R> using acc_t = typename CGAcc<R>::T;
-
 template <class R> __device__ __forceinline__ acc_t<R> acc_zero() { return 0.0; }
 template <> __device__ __forceinline__ FF acc_zero<float>() { return {0.f, 0.f}; }
 template <class R> __device__ __forceinline__ acc_t<R> acc_dot3(V3<R> a, V3<R> b) {
@@ -162,13 +165,122 @@ __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   return x;
 }
-// warp sum, valid in lane 0, as a double
+// warp sum (valid in lane 0), sum, broadcast of lane 0
 __device__ __forceinline__ double acc_warp_total(double x) { return warp_sum(x); }
-__device__ __forceinline__ double acc_warp_total(FF x) { return ff_to_double(ff_warp_sum(x)); }
+__device__ __forceinline__ FF acc_warp_total(FF x) { return ff_warp_sum(x); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ FF acc_add(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ double acc_bcast0(double x) { return __shfl_sync(0xffffffffu, x, 0); }
+__device__ __forceinline__ FF acc_bcast0(FF x) {
+  return {__shfl_sync(0xffffffffu, x.hi, 0), __shfl_sync(0xffffffffu, x.lo, 0)};
+}
+__device__ __forceinline__ bool acc_finite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool acc_finite(FF x) { return isfinite(x.hi) && isfinite(x.lo); }
 
-// alpha of a sheet in the form the solution update takes
+// alpha and beta of a sheet in the form the row kernels take
 template <class R> __device__ __forceinline__ acc_t<R> alpha_of(const CGSheet& c) { return c.alpha; }
-template <> __device__ __forceinline__ FF alpha_of<float>(const CGSheet& c) { return {c.alpha_hi, c.alpha_lo}; }
+template <> __device__ __forceinline__ FF alpha_of<float>(const CGSheet& c) { return c.alpha_f; }
+template <class R> __device__ __forceinline__ R beta_of(const CGSheet& c) { return (R)c.beta; }
+template <> __device__ __forceinline__ float beta_of<float>(const CGSheet& c) { return c.beta_f; }
+
+// ------------------------------------------------------------------ CG scalar steps
+// Shared by the device loop's per-sheet scalar kernels and the per-sheet solver, so both
+// form alpha, beta and the stopping decisions bitwise alike.  Each returns true when the
+// sheet's solve is over (converged, or stopped with a status bit).
+// After the initial sums r.z, r.r (b = r at the start).
+template <class R> __device__ __forceinline__ bool cg_init_step(CGSheet& c, acc_t<R> rz, acc_t<R> rr, double tol);
+template <> __device__ __forceinline__ bool cg_init_step<double>(CGSheet& c, double rz, double rr, double tol) {
+  c.rz = rz;
+  c.rr = rr;
+  c.bb = rr;
+  c.stop_rr = tol * tol * rr;
+  c.beta = 0.0;
+  c.iters = 0;
+  c.done = 0;
+  if (!isfinite(rr)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    return true;
+  }
+  return rr == 0.0 || rr <= c.stop_rr;
+}
+template <> __device__ __forceinline__ bool cg_init_step<float>(CGSheet& c, FF rz, FF rr, double tol) {
+  const double rrd = ff_to_double(rr);
+  c.rz = ff_to_double(rz);
+  c.rr = rrd;
+  c.bb = rrd;
+  c.stop_rr = tol * tol * rrd;
+  c.rz_f = rz;
+  c.stop_f = ff_from_double(c.stop_rr);
+  c.beta = 0.0;
+  c.beta_f = 0.f;
+  c.iters = 0;
+  c.done = 0;
+  if (!acc_finite(rr)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    return true;
+  }
+  return rr.hi == 0.f || ff_le(rr, c.stop_f);
+}
+// After the sum p.Ap: alpha = r.z / p.Ap.
+template <class R> __device__ __forceinline__ bool cg_alpha_step(CGSheet& c, acc_t<R> pAp);
+template <> __device__ __forceinline__ bool cg_alpha_step<double>(CGSheet& c, double pAp) {
+  c.pAp = pAp;
+  if (!isfinite(pAp)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    return true;
+  }
+  if (pAp <= 0.0) {
+    c.status |= CLOTH_STATUS_INDEFINITE;
+    return true;
+  }
+  c.alpha = c.rz / pAp;
+  return false;
+}
+template <> __device__ __forceinline__ bool cg_alpha_step<float>(CGSheet& c, FF pAp) {
+  if (!acc_finite(pAp)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    return true;
+  }
+  if (pAp.hi <= 0.f) {
+    c.status |= CLOTH_STATUS_INDEFINITE;
+    return true;
+  }
+  c.alpha_f = ff_div(c.rz_f, pAp);
+  return false;
+}
+// After the update's sums r.z, r.r: beta = r.z / previous r.z, one iteration done.
+template <class R> __device__ __forceinline__ bool cg_beta_step(CGSheet& c, acc_t<R> rz, acc_t<R> rr, int maxit);
+template <> __device__ __forceinline__ bool cg_beta_step<double>(CGSheet& c, double rz, double rr, int maxit) {
+  c.beta = rz / c.rz;
+  c.rz = rz;
+  c.rr = rr;
+  c.iters += 1;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    return true;
+  }
+  if (rr <= c.stop_rr) return true;
+  if (c.iters >= maxit) {
+    c.status |= CLOTH_STATUS_CG_MAXITER;
+    return true;
+  }
+  return false;
+}
+template <> __device__ __forceinline__ bool cg_beta_step<float>(CGSheet& c, FF rz, FF rr, int maxit) {
+  c.beta_f = ff_div(rz, c.rz_f).hi;
+  c.rz_f = rz;
+  c.iters += 1;
+  if (!acc_finite(rr) || !acc_finite(rz)) {
+    c.status |= CLOTH_STATUS_NONFINITE;
+    return true;
+  }
+  if (ff_le(rr, c.stop_f)) return true;
+  if (c.iters >= maxit) {
+    c.status |= CLOTH_STATUS_CG_MAXITER;
+    return true;
+  }
+  return false;
+}
 __device__ __forceinline__ double alpha_cast(double a) { return a; }
 __device__ __forceinline__ float alpha_cast(FF a) { return a.hi; }  // = (float) alpha
 
@@ -655,7 +767,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
       v0 = acc_dot3(r, z);
       v1 = acc_dot3(r, r);
     }
-    const double t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
+    const acc_t<R> t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
     if (lane == 0) {
       d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
       d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
@@ -665,38 +777,22 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
 
 // Sum over the warp partials of sheet s (one warp, lane-strided then shuffle tree).
 template <class R>
-__device__ __forceinline__ double sheet_sum(const Dev<R>& d, const double* part, int s) {
+__device__ __forceinline__ acc_t<R> sheet_sum(const Dev<R>& d, const acc_t<R>* part, int s) {
   const int lane = threadIdx.x & 31;
   const int p0 = d.sheet_wfirst[s] * kWarpsPerEntry, p1 = d.sheet_wfirst[s + 1] * kWarpsPerEntry;
-  double acc = 0.0;
-  for (int q = p0 + lane; q < p1; q += 32) acc += part[q];
-  acc = warp_sum(acc);
-  return __shfl_sync(0xffffffffu, acc, 0);
+  acc_t<R> acc = acc_zero<R>();
+  for (int q = p0 + lane; q < p1; q += 32) acc = acc_add(acc, part[q]);
+  return acc_bcast0(acc_warp_total(acc));
 }
 
-// Per sheet after k_cg_init: rz, rr, bb; a sheet with b = 0 (or non-finite) is done at once.
+// Per sheet after k_cg_init: r.z, r.r, |b|^2; a sheet with b = 0 (or non-finite) is done at once.
 template <class R>
 __global__ void k_cg_scalar_init(Dev<R> d, int phase) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (s >= d.S) return;
-  const double rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
+  const acc_t<R> rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
   if ((threadIdx.x & 31) != 0) return;
-  CGSheet& c = d.cg[s];
-  c.rz = rz;
-  c.rr = rr;
-  c.bb = rr;
-  c.stop_rr = d.tol * d.tol * rr;
-  c.beta = 0.0;
-  c.iters = 0;
-  c.done = 0;
-  bool fin = false;
-  if (!isfinite(rr)) {
-    c.status |= CLOTH_STATUS_NONFINITE;
-    fin = true;
-  } else if (rr == 0.0 || rr <= c.stop_rr) {
-    fin = true;
-  }
-  if (fin) finish_sheet(d, s, phase, 0, 0);
+  if (cg_init_step<R>(d.cg[s], rz, rr, d.tol)) finish_sheet(d, s, phase, 0, 0);
 }
 
 // One row of the SpMV: Ap_i = (A p_k)_i in difference form; returns p_i . Ap_i (or 0).
@@ -792,17 +888,17 @@ __device__ __forceinline__ const R* pbuf(const Dev<R>& d, int parity) {
 
 // Ap = A p_k over all active sheets; warp partials of p.Ap.
 template <class R, bool FUSED>
-__global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
+__global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_cg_spmv(Dev<R> d) {
   const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
     const int s = d.work_sheet[w];
     if (d.cg[s].done) continue;  // uniform over the CTA
     const int k = d.cg[s].iters;
-    const R beta = (R)d.cg[s].beta;
+    const R beta = beta_of<R>(d.cg[s]);
     acc_t<R> v = acc_zero<R>();
     if (threadIdx.x < d.work_rows[w])
       v = spmv_row<R, FUSED>(d, d.work_row0[w] + threadIdx.x, beta, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
-    const double t = acc_warp_total(v);
+    const acc_t<R> t = acc_warp_total(v);
     if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = t;
   }
 }
@@ -812,22 +908,9 @@ template <class R>
 __global__ void k_cg_scalar_alpha(Dev<R> d, int phase, cudaGraphConditionalHandle cond, int use_cond) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (s >= d.S || d.cg[s].done) return;  // uniform over the warp
-  const double pAp = sheet_sum(d, d.part_c, s);
+  const acc_t<R> pAp = sheet_sum(d, d.part_c, s);
   if ((threadIdx.x & 31) != 0) return;
-  CGSheet& c = d.cg[s];
-  c.pAp = pAp;
-  if (!isfinite(pAp)) {
-    c.status |= CLOTH_STATUS_NONFINITE;
-    finish_sheet(d, s, phase, cond, use_cond);
-  } else if (pAp <= 0.0) {
-    c.status |= CLOTH_STATUS_INDEFINITE;
-    finish_sheet(d, s, phase, cond, use_cond);
-  } else {
-    c.alpha = c.rz / pAp;
-    const FF a = ff_from_double(c.alpha);
-    c.alpha_hi = a.hi;
-    c.alpha_lo = a.lo;
-  }
+  if (cg_alpha_step<R>(d.cg[s], pAp)) finish_sheet(d, s, phase, cond, use_cond);
 }
 
 // dv += alpha p_k (FP64), r -= alpha Ap, z = D^{-1} r (stored); warp partials of r.z, r.r.
@@ -841,7 +924,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d) {
     acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>();
     if (threadIdx.x < d.work_rows[w])
       update_row(d, d.work_row0[w] + threadIdx.x, alpha_of<R>(d.cg[s]), pbuf(d, k), v0, v1);
-    const double t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
+    const acc_t<R> t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
     if (lane_w == 0) {
       d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
       d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
@@ -856,22 +939,9 @@ __global__ void k_cg_scalar_beta(Dev<R> d, int phase, cudaGraphConditionalHandle
   if (blockIdx.x == 0 && threadIdx.x == 0) d.body_runs[phase] += 1ull;
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (s >= d.S || d.cg[s].done) return;
-  const double rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
+  const acc_t<R> rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
   if ((threadIdx.x & 31) != 0) return;
-  CGSheet& c = d.cg[s];
-  c.beta = rz / c.rz;
-  c.rz = rz;
-  c.rr = rr;
-  c.iters += 1;
-  if (!isfinite(rr) || !isfinite(rz)) {
-    c.status |= CLOTH_STATUS_NONFINITE;
-    finish_sheet(d, s, phase, cond, use_cond);
-  } else if (rr <= c.stop_rr) {
-    finish_sheet(d, s, phase, cond, use_cond);
-  } else if (c.iters >= d.maxit) {
-    c.status |= CLOTH_STATUS_CG_MAXITER;
-    finish_sheet(d, s, phase, cond, use_cond);
-  }
+  if (cg_beta_step<R>(d.cg[s], rz, rr, d.maxit)) finish_sheet(d, s, phase, cond, use_cond);
 }
 
 // p_{k+1} = z_{k+1} + beta_{k+1} p_k (separate-direction schedule), after k_cg_scalar_beta
@@ -882,7 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
     if (d.cg[s].done) continue;
     if (threadIdx.x >= d.work_rows[w]) continue;
     const int k = d.cg[s].iters;  // already k + 1
-    const R beta = (R)d.cg[s].beta;
+    const R beta = beta_of<R>(d.cg[s]);
     const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
     R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
     const int i = d.work_row0[w] + threadIdx.x;
@@ -904,9 +974,6 @@ __global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
 // order, so all take the same branches.  The arithmetic and the summation orders are those
 // of the device loop above, so the results are bitwise the same.
 constexpr int kColCache = 16;  // column indices kept in registers per row (further slots are loaded)
-
-template <class R> __device__ __forceinline__ acc_t<R> acc_from_double(double x) { return x; }
-template <> __device__ __forceinline__ FF acc_from_double<float>(double x) { return ff_from_double(x); }
 
 // CG solution of one row in registers: FP64, or float-float in FP32 mode
 template <class R> struct DvReg {
@@ -959,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   if (d.cg[s].done) return;  // uniform: written only at the end of this sheet's solve
 
   // partial sums of the CTA's warps: [0] p.Ap, [1] r.z, [2] r.r, per local entry and warp
-  __shared__ double sp[3][EPC][kWarpsPerEntry];
+  __shared__ acc_t<R> sp[3][EPC][kWarpsPerEntry];
   __shared__ acc_t<R> bc_alpha;
   __shared__ R bc_beta;
   __shared__ int bc_stop;
@@ -978,20 +1045,20 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   // the sheet's sum of one partial array, in the order of sheet_sum (lane-strided, then a
   // shuffle tree); called by one full warp
   auto sheet_total = [&](int which) {
-    double acc = 0.0;
+    acc_t<R> acc = acc_zero<R>();
     for (int q = w0 * kWarpsPerEntry + lane; q < w1 * kWarpsPerEntry; q += 32) {
       const int e = q / kWarpsPerEntry - w0, pw = q % kWarpsPerEntry;
       const int rk = e % CL, jj = e / CL;
-      const double* src = &sp[which][jj][pw];
+      const acc_t<R>* src = &sp[which][jj][pw];
       if (CL > 1) src = cgrp::this_cluster().map_shared_rank(src, rk);
-      acc += *src;
+      acc = acc_add(acc, *src);
     }
-    return warp_sum(acc);
+    return acc_warp_total(acc);
   };
 
   // row state
   int k = d.cg[s].iters;
-  R beta_r = (R)d.cg[s].beta;
+  R beta_r = beta_of<R>(d.cg[s]);
   V3<R> r = {R(0), R(0), R(0)}, z = r, pold = r, Ap = r;
   DvReg<R> x;
   int K = 0, base = 0, col[kColCache];
@@ -1007,10 +1074,8 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   }
 #pragma unroll
   for (int q = 0; q < kColCache; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
-  // thread 0's copy of the sheet's scalars
-  double rz = d.cg[s].rz, beta = d.cg[s].beta, rr = d.cg[s].rr, pAp = 0.0, al = 0.0;
-  const double stop_rr = d.cg[s].stop_rr;
-  int status = 0;
+  // thread 0's copy of the sheet's scalars, advanced by the loop's scalar steps
+  CGSheet c = d.cg[s];
 
   while (true) {
     // ---- Ap = A p_k, p_k = z_k + beta_k p_{k-1} formed on the fly (own row and neighbours)
@@ -1050,26 +1115,15 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
       vpart = acc_dot3(pi, y);
     }
     {
-      const double tw = acc_warp_total(vpart);
+      const acc_t<R> tw = acc_warp_total(vpart);
       if (lane == 0) sp[0][jl][wp] = tw;
     }
     barrier();
     if (threadIdx.x < 32) {
-      const double tsum = sheet_total(0);
+      const acc_t<R> tsum = sheet_total(0);
       if (threadIdx.x == 0) {
-        pAp = tsum;
-        int stop = 0;
-        if (!isfinite(pAp)) {
-          status |= CLOTH_STATUS_NONFINITE;
-          stop = 1;
-        } else if (pAp <= 0.0) {
-          status |= CLOTH_STATUS_INDEFINITE;
-          stop = 1;
-        } else {
-          al = rz / pAp;
-        }
-        bc_alpha = acc_from_double<R>(al);
-        bc_stop = stop;
+        bc_stop = cg_alpha_step<R>(c, tsum);
+        bc_alpha = alpha_of<R>(c);
       }
     }
     __syncthreads();
@@ -1093,7 +1147,7 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
       pold = pi;
     }
     {
-      const double ta = acc_warp_total(va), tb = acc_warp_total(vb);
+      const acc_t<R> ta = acc_warp_total(va), tb = acc_warp_total(vb);
       if (lane == 0) {
         sp[1][jl][wp] = ta;
         sp[2][jl][wp] = tb;
@@ -1102,23 +1156,10 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
     barrier();
     k += 1;
     if (threadIdx.x < 32) {
-      const double a = sheet_total(1), b = sheet_total(2);
+      const acc_t<R> a = sheet_total(1), b = sheet_total(2);
       if (threadIdx.x == 0) {
-        rr = b;
-        beta = a / rz;
-        rz = a;
-        int stop = 0;
-        if (!isfinite(rr) || !isfinite(a)) {
-          status |= CLOTH_STATUS_NONFINITE;
-          stop = 1;
-        } else if (rr <= stop_rr) {
-          stop = 1;
-        } else if (k >= d.maxit) {
-          status |= CLOTH_STATUS_CG_MAXITER;
-          stop = 1;
-        }
-        bc_beta = (R)beta;
-        bc_stop = stop;
+        bc_stop = cg_beta_step<R>(c, a, b, d.maxit);
+        bc_beta = beta_of<R>(c);
       }
     }
     __syncthreads();
@@ -1133,17 +1174,7 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   // no CTA leaves while another may still read its shared memory
   if (CL > 1) cgrp::this_cluster().sync();
   if (rank == 0 && threadIdx.x == 0) {
-    CGSheet& c = d.cg[s];
-    c.iters = k;
-    c.rz = rz;
-    c.rr = rr;
-    c.beta = beta;
-    c.alpha = al;
-    const FF af = ff_from_double(al);
-    c.alpha_hi = af.hi;
-    c.alpha_lo = af.lo;
-    c.pAp = pAp;
-    c.status |= status;
+    d.cg[s] = c;
     finish_sheet(d, s, phase, 0, 0);
   }
 }

@@ -2,9 +2,9 @@
 //
 // A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2, about 48
 // significant bits.  GB300 issues FP64 arithmetic at a small fraction of its FP32 rate, so
-// the FP32 mode's CG keeps its in-warp dot-product sums and its solution accumulator in
-// this form and turns to FP64 only once per warp (the partial sums, added over warps in
-// FP64) and once per solve (the solution vector).
+// the FP32 mode's CG keeps its dot-product sums, its scalars (r.z, alpha, the stopping
+// threshold) and its solution accumulator in this form, and turns to FP64 only once per
+// solve (the solution vector and the diagnostic copies of the scalars).
 //
 // Addition: Knuth's two-sum of the high parts, the low parts added to its error, then a
 // fast two-sum renormalisation (Dekker 1971; the "sloppy" double-double addition of Hida,
@@ -46,6 +46,21 @@ __host__ __device__ __forceinline__ FF ff_from_double(double x) {
 }
 
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+
+// a / b: float quotient, its remainder a - q1 b formed in float-float, one correction term
+// (the double-double division of Hida, Li and Bailey, carried out on float pairs)
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const FF r = ff_add(a, ff_neg(ff_mul(b, q1)));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  const float hi = __fadd_rn(q1, q2);
+  return {hi, __fsub_rn(q2, __fsub_rn(hi, q1))};
+}
+
+// a <= b for normalised pairs
+__device__ __forceinline__ bool ff_le(FF a, FF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
 
 __device__ __forceinline__ FF ff_warp_sum(FF x) {
 #pragma unroll
