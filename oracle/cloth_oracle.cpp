@@ -693,11 +693,14 @@ void oracle_system_matvec(void* h, const double* material, double eta, double dt
 }
 
 // Forward trajectory.  x0, v0: [n][3]; forces: [steps][n][3] or NULL;
-// traj_x, traj_v: [steps+1][n][3]; dv_out [steps][n][3] or NULL; cg_iters [steps];
+// force_mode 0: F_t is a force [N] added to f (Eq. 3); 1: F_t is a velocity increment
+// [m/s] added to the free vertices' velocities before step t (the corrective forces'
+// form in the paper's experiments), v'_t = v_t + F_t, and the step runs from (x_t, v'_t).
+// traj_x, traj_v: [steps+1][n][3] (traj_v holds v_t, before any increment); cg_iters [steps];
 // status: worst per-step solver status (0 ok, 1 maxiter, 2 indefinite, 3 non-finite).
 int oracle_forward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,
                    int max_iter, const double* gravity, const double* x0, const double* v0, const double* forces,
-                   double* traj_x, double* traj_v, int* cg_iters, int* status) {
+                   int force_mode, double* traj_x, double* traj_v, int* cg_iters, int* status) {
   const Sim* s = static_cast<Sim*>(h);
   Mat mt{material[0], material[1], material[2], material[3], eta, precond};
   const int N = 3 * s->n;
@@ -712,12 +715,15 @@ int oracle_forward(void* h, const double* material, double eta, int precond, dou
     Sparse Hm(N), Hb(N);
     internal_hessian(*s, mt, x, Hm, Hb);
     internal_forces(*s, mt, x, fm.data(), fb.data(), nullptr);
-    std::vector<double> vv(v, v + N);
+    std::vector<double> vv(v, v + N);  // the step's starting velocity
+    if (F && force_mode == 1)
+      for (int i = 0; i < N; ++i)
+        if (!s->pinned[i / 3]) vv[i] += F[i];
     Hm.matvec(vv, Hv);
     Hb.matvec(vv, Hv2);
     for (int i = 0; i < N; ++i) {
       const int vi = i / 3;
-      double f = fm[i] + fb[i] + mt.rho * s->area3[vi] * gravity[i % 3] + (F ? F[i] : 0.0);
+      double f = fm[i] + fb[i] + mt.rho * s->area3[vi] * gravity[i % 3] + (F && force_mode == 0 ? F[i] : 0.0);
       b[i] = s->pinned[vi] ? 0.0 : dt * (f - dt * (Hv[i] + Hv2[i]));
     }
     Sparse A = system_matrix(*s, mt, dt, Hm, Hb);
@@ -728,7 +734,7 @@ int oracle_forward(void* h, const double* material, double eta, int precond, dou
     double* xn = traj_x + (size_t)(t + 1) * N;
     double* vn = traj_v + (size_t)(t + 1) * N;
     for (int i = 0; i < N; ++i) {
-      vn[i] = v[i] + dv[i];
+      vn[i] = vv[i] + dv[i];
       xn[i] = x[i] + dt * vn[i];
     }
   }
@@ -741,10 +747,12 @@ int oracle_forward(void* h, const double* material, double eta, int precond, dou
 // dL_dx: [steps+1][n][3] (gradient of the loss w.r.t. every x_t, t = 0..steps).
 // Outputs (any may be NULL): g_material[4] (dL/dY, dL/dnu := 0, dL/dkb, dL/drho),
 // g_forces [steps][n][3], g_x0 [n][3], g_v0 [n][3]; cg_iters [steps]; status.
+// forces, force_mode: as given to oracle_forward (the forces are read only in mode 1,
+// where the step started from v'_t = v_t + F_t; then dL/dF_t = dL/dv'_t on free vertices).
 int oracle_backward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,
                     int max_iter, const double* gravity, const double* traj_x, const double* traj_v,
-                    const double* dL_dx, double* g_material, double* g_forces, double* g_x0, double* g_v0,
-                    int* cg_iters, int* status) {
+                    const double* forces, int force_mode, const double* dL_dx, double* g_material,
+                    double* g_forces, double* g_x0, double* g_v0, int* cg_iters, int* status) {
   const Sim* s = static_cast<Sim*>(h);
   Mat mt{material[0], material[1], material[2], material[3], eta, precond};
   const int N = 3 * s->n;
@@ -756,9 +764,11 @@ int oracle_backward(void* h, const double* material, double eta, int precond, do
     const double* x = traj_x + (size_t)t * N;
     const double* v = traj_v + (size_t)t * N;
     const double* vn = traj_v + (size_t)(t + 1) * N;
+    const double* F = (forces && force_mode == 1) ? forces + (size_t)t * N : nullptr;
     for (int i = 0; i < N; ++i) {
       u[i] = vn[i];
-      dv[i] = vn[i] - v[i];
+      const double vstart = v[i] + ((F && !s->pinned[i / 3]) ? F[i] : 0.0);  // v'_t
+      dv[i] = vn[i] - vstart;
       // adjoint of dv: v_{t+1} = v_t + dv and x_{t+1} = x_t + h v_{t+1}
       g[i] = s->pinned[i / 3] ? 0.0 : av[i] + dt * ax[i];
     }
@@ -793,13 +803,14 @@ int oracle_backward(void* h, const double* material, double eta, int precond, do
       const double Klam = -(Hl[i] + Hl2[i]);       // K~ lambda (matrix of the solve)
       const double Kxlam = -(Hxl[i] + Hxl2[i]);    // K lambda, exact force Jacobian
       const double vtot = av[i] + dt * ax[i];
-      if (g_forces) g_forces[(size_t)t * N + i] = dt * lam[i];
+      if (g_forces && force_mode == 0) g_forces[(size_t)t * N + i] = dt * lam[i];
       // parameters: dL/dp += lam^T (db/dp - dA/dp dv)
       gY += lam[i] * (dt * fm[i] - dt * dt * Hu[i]) / mt.Y;     // f_mem, K_mem linear in Y
       gkb += lam[i] * (dt * fb[i] - dt * dt * Hu2[i]) / mt.kb;  // f_bend, K_bend linear in kb
       grho += lam[i] * s->area3[i / 3] * (dt * gravity[i % 3] - dv[i]);
       ax[i] = ax[i] + dt * Kxlam - dt * dt * third[i] + dL_dx[(size_t)t * N + i];
-      av[i] = vtot + dt * dt * Klam;
+      av[i] = vtot + dt * dt * Klam;  // adjoint of the step's starting velocity (= of v_t)
+      if (g_forces && force_mode == 1) g_forces[(size_t)t * N + i] = s->pinned[i / 3] ? 0.0 : av[i];
     }
   }
   if (g_material) {

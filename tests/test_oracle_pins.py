@@ -310,6 +310,49 @@ def test_free_fall_closed_form(oracle_mod):
         np.testing.assert_allclose(tx[t], rest + dt * dt * g * t * (t + 1) / 2, atol=1e-9)
 
 
+def test_velocity_increments_free_fall_closed_form(oracle_mod):
+    """Corrective forces as velocity increments: an unpinned sheet at rest receiving the
+    same increment c at every vertex and step moves rigidly (K annihilates uniform
+    motion), so v_{t+1} = v_t + c + h g, i.e. v_t = t (c + h g) and
+    x_t = x_0 + h (c + h g) t (t+1)/2; as a force (mode 0) the same c gives h c / m per step."""
+    sim, rest = _small_sheet(oracle_mod, 6, "none")
+    dt, T = 1.0 / 30.0, 10
+    c = np.array([0.02, -0.01, 0.03])
+    F = np.broadcast_to(c, (T, sim.n, 3)).copy()
+    tx, tv, _, st = sim.forward(MAT, rest, np.zeros_like(rest), F, dt=dt, steps=T, tol=1e-12, max_iter=1000,
+                                gravity=W.GRAVITY, force_mode=1)
+    assert st == 0
+    w = c + dt * np.array(W.GRAVITY)
+    for t in range(T + 1):
+        np.testing.assert_allclose(tv[t], np.broadcast_to(t * w, rest.shape), atol=1e-9)
+        np.testing.assert_allclose(tx[t], rest + dt * w * t * (t + 1) / 2, atol=1e-9)
+    tx0, _, _, _ = sim.forward(MAT, rest, np.zeros_like(rest), F, dt=dt, steps=T, tol=1e-12, max_iter=1000,
+                               gravity=W.GRAVITY, force_mode=0)
+    assert np.abs(tx0[-1] - tx[-1]).max() > 1e-3  # the two readings differ
+
+
+def test_velocity_increments_ignore_pinned_vertices(oracle_mod):
+    """Increments on pinned vertices change nothing (pins are kinematic), in both the
+    trajectory and the gradients; their force gradients are zero."""
+    rng = np.random.default_rng(5)
+    sim, rest = _small_sheet(oracle_mod, 5, "top2")
+    pin = W.pins(5, "top2").astype(bool)
+    dt, T = 1.0 / 30.0, 5
+    F = 1e-2 * rng.normal(size=(T, sim.n, 3))
+    Fm = F.copy()
+    Fm[:, pin] = 0.0
+    kw = dict(dt=dt, steps=T, tol=1e-13, max_iter=5000, gravity=W.GRAVITY)
+    tx, tv, _, _ = sim.forward(MAT, rest, np.zeros_like(rest), F, force_mode=1, **kw)
+    txm, tvm, _, _ = sim.forward(MAT, rest, np.zeros_like(rest), Fm, force_mode=1, **kw)
+    np.testing.assert_array_equal(tx, txm)
+    np.testing.assert_array_equal(tv, tvm)
+    dL = rng.normal(size=tx.shape)
+    g = sim.backward(MAT, tx, tv, dL, forces=F, force_mode=1, **kw)
+    gm = sim.backward(MAT, txm, tvm, dL, forces=Fm, force_mode=1, **kw)
+    np.testing.assert_array_equal(g["material"], gm["material"])
+    assert np.all(g["forces"][:, pin] == 0.0)
+
+
 def test_implicit_euler_dissipates_energy_linear_regime(oracle_mod):
     """Backward Euler on a linear elastic system with SPD stiffness dissipates the
     energy 1/2 v^T M v + 1/2 u^T H u at every step.  A tiny in-plane perturbation of
@@ -361,8 +404,9 @@ def test_loss_l2_and_pinhole(oracle_mod):
 
 
 # ----------------------------------------------------------------- adjoint
-def _rollout_loss(sim, mat, x0, v0, F, target, dt, T, tol):
-    tx, tv, _, st = sim.forward(mat, x0, v0, F, dt=dt, steps=T, tol=tol, max_iter=20000, gravity=W.GRAVITY)
+def _rollout_loss(sim, mat, x0, v0, F, target, dt, T, tol, force_mode=0):
+    tx, tv, _, st = sim.forward(mat, x0, v0, F, dt=dt, steps=T, tol=tol, max_iter=20000, gravity=W.GRAVITY,
+                                force_mode=force_mode)
     from oracle import loss_l2
     return loss_l2(tx, target)[0], tx, tv
 
@@ -416,4 +460,44 @@ def test_adjoint_matches_finite_differences(oracle_mod, N, T):
             name = {"forces": "F", "x0": "x0", "v0": "v0"}[key]
             args[name] = args[name] + e * d
             return _rollout_loss(sim, mat, args["x0"], args["v0"], args["F"], target, dt, T, tol)[0]
+        check(_richardson(f, 1e-3 * scale), float((gr[key] * d).sum()), key)
+
+
+def test_adjoint_velocity_increments_matches_finite_differences(oracle_mod):
+    """Corrective forces as velocity increments (v'_t = v_t + F_t before each step): the
+    adjoint's gradients w.r.t. Y, kb, rho, the increments, x0 and v0 against Richardson-
+    extrapolated central differences of the forward map."""
+    rng = np.random.default_rng(31)
+    N, T = 4, 6
+    rest, tris = W.grid_mesh(N)
+    pin = W.pins(N, "top2")
+    sim = oracle_mod.OracleSim(rest, tris, pin)
+    dt, tol = 1.0 / 30.0, 1e-13
+    mat = MAT.copy()
+    F = 1e-3 * rng.normal(size=(T, sim.n, 3))
+    x0 = rest.copy()
+    v0 = np.zeros_like(rest)
+    target, _, _, _ = sim.forward(mat * np.array([2.0, 1.0, 0.5, 1.0]), x0, v0, F, dt=dt, steps=T, tol=tol,
+                                  max_iter=20000, gravity=W.GRAVITY, force_mode=1)
+    L, tx, tv = _rollout_loss(sim, mat, x0, v0, F, target, dt, T, tol, force_mode=1)
+    _, dL = oracle_mod.loss_l2(tx, target)
+    gr = sim.backward(mat, tx, tv, dL, dt=dt, steps=T, tol=tol, max_iter=20000, gravity=W.GRAVITY, forces=F,
+                      force_mode=1)
+    assert gr["status"] == 0
+
+    def check(fd, an, what):
+        assert an == pytest.approx(fd, rel=2e-6, abs=1e-9 * max(1.0, abs(L))), what
+
+    for k, name in ((0, "Y"), (2, "kb"), (3, "rho")):
+        def f(e, k=k):
+            m2 = mat.copy(); m2[k] += e
+            return _rollout_loss(sim, m2, x0, v0, F, target, dt, T, tol, force_mode=1)[0]
+        check(_richardson(f, 1e-3 * mat[k]), gr["material"][k], name)
+    free = (pin == 0)[:, None].astype(float)
+    for d, key, scale in ((rng.normal(size=F.shape) * free, "forces", 1e-3), (rng.normal(size=rest.shape), "x0", 1e-3),
+                          (rng.normal(size=rest.shape) * free, "v0", 1e-3)):
+        def f(e, d=d, key=key):
+            a = {"forces": F, "x0": x0, "v0": v0}
+            a[key] = a[key] + e * d
+            return _rollout_loss(sim, mat, a["x0"], a["v0"], a["forces"], target, dt, T, tol, force_mode=1)[0]
         check(_richardson(f, 1e-3 * scale), float((gr[key] * d).sum()), key)
