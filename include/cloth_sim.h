@@ -99,7 +99,17 @@ typedef struct cloth_opts {
                                0 = chosen by the autotuner (cg_schedule = -1: timed
                                whole solves of the loop alone and of hand-overs at
                                count/16 ... count), or every sheet (explicit schedule) */
+  int32_t force_mode;       /* how the per-step per-vertex input F_t of cloth_forward
+                               acts: CLOTH_FORCES_FORCE (a force [N] added to f, Eq. 3)
+                               or CLOTH_FORCES_VELOCITY (a velocity increment [m/s]
+                               added to the free vertices' velocities before step t,
+                               the form the paper's corrective forces take in its
+                               experiments, Sec. 4); the backward then returns dL/dF_t
+                               in the same sense                                      */
 } cloth_opts;
+
+#define CLOTH_FORCES_FORCE 0
+#define CLOTH_FORCES_VELOCITY 1
 
 #define CLOTH_PRECOND_JACOBI 0
 #define CLOTH_PRECOND_BLOCK_JACOBI 1
@@ -135,8 +145,9 @@ int cloth_batch_info(const cloth_batch* batch, int32_t* total_vertices, int32_t*
 
 /* Forward trajectory (Eq. 1, Eq. 3-5), all sheets at once.
  * material: device [count][4] = (Y [N/m], nu, k_b [N m], rho [kg/m^2]) per sheet;
- * x0, v0: device [N_total][3]; forces: device [steps][N_total][3] newtons, or NULL
- * for none; traj_x: device [steps + 1][N_total][3], written (traj_x[0] = x0);
+ * x0, v0: device [N_total][3]; forces: device [steps][N_total][3] newtons (or m/s
+ * velocity increments under CLOTH_FORCES_VELOCITY, see cloth_opts.force_mode), or
+ * NULL for none; traj_x: device [steps + 1][N_total][3], written (traj_x[0] = x0);
  * status: device [count] int32, written with CLOTH_STATUS_* bits.
  * Keeps internally what cloth_backward needs: a copy of `material` and the
  * checkpointed states.  `forces` is read again by the backward's recompute, so its
@@ -207,7 +218,8 @@ int cloth_internal_forces(cloth_batch* batch, const void* material, const void* 
                           void* f_membrane, void* f_bending, void* stream);
 
 /* The linear system of one step (Eq. 4-5) at state (x, v) with external force
- * F (device [N_total][3] or NULL), assembled by the step kernels and expanded to
+ * F (device [N_total][3] or NULL; under CLOTH_FORCES_VELOCITY a velocity increment,
+ * the step then starting from v + F), assembled by the step kernels and expanded to
  * dense per sheet: A: device [sum_s (3 n_s)^2] (sheet blocks one after another,
  * row-major, user vertex order), b: device [N_total][3].  Pinned rows and
  * columns are identity, b = 0 there.  For small sheets (testing). */

@@ -55,6 +55,7 @@ void cloth_default_opts(cloth_opts* o) {
   o->precond = CLOTH_PRECOND_BLOCK_JACOBI;
   o->cg_schedule = -1;
   o->cg_handover = 0;
+  o->force_mode = CLOTH_FORCES_FORCE;
 }
 
 int cloth_mesh_create(const double* rest_xyz, int32_t n, const int32_t* tris, int32_t m, const uint8_t* pinned,
@@ -93,7 +94,8 @@ int cloth_batch_create(const cloth_mesh* const* meshes, int32_t count, const clo
   if (o.steps < 1 || !(o.dt > 0.0) || !(o.cg_tol >= 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 ||
       !(o.clamp_eta >= 0.0) || (o.exec != CLOTH_EXEC_PLAIN && o.exec != CLOTH_EXEC_GRAPH) || o.cg_poll_every < 1 ||
       (o.precond != CLOTH_PRECOND_JACOBI && o.precond != CLOTH_PRECOND_BLOCK_JACOBI) || o.cg_schedule < -1 ||
-      o.cg_schedule > 7 || o.cg_handover < 0)
+      o.cg_schedule > 7 || o.cg_handover < 0 ||
+      (o.force_mode != CLOTH_FORCES_FORCE && o.force_mode != CLOTH_FORCES_VELOCITY))
     return fail(CLOTH_ERR_INVALID_ARG, "cloth_batch_create: invalid option value");
   std::vector<const cloth::MeshData*> sheets;
   for (int i = 0; i < count; ++i) {

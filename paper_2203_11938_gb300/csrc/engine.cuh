@@ -1179,6 +1179,21 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   }
 }
 
+// Velocity increments: out = v + F_t on free vertices (F_t in the user layout), v elsewhere.
+template <class R>
+__global__ void k_add_increment(Dev<R> d, const double* __restrict__ v, const R* __restrict__ F,
+                                double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  V3<double> w = ld3(v, i);
+  const int u = d.i2u[i];
+  if (u >= 0 && !d.pinned[i]) {
+    const V3<R> f = ld3(F, u);
+    w = {w.x + (double)f.x, w.y + (double)f.y, w.z + (double)f.z};
+  }
+  st3(out, i, w);
+}
+
 // v' = v + dv, x' = x + h v'; optional user-layout copy of x'.
 template <class R>
 __global__ void k_state_update(Dev<R> d, const double* __restrict__ x, const double* __restrict__ v,
@@ -1328,9 +1343,12 @@ __global__ void k_adj_rhs(Dev<R> d, const double* __restrict__ ax, const double*
 }
 
 // Per-vertex adjoint update after the element pass; lam = d.dv.
+// v_t: the velocity the step started from; fmode 0: gF = h lam (F_t a force), 1: gF = the
+// adjoint of the starting velocity on free vertices (F_t a velocity increment).
 template <class R>
 __global__ void k_adj_vertex(Dev<R> d, double* __restrict__ ax, double* __restrict__ av, const double* __restrict__ v_t,
-                             const double* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row) {
+                             const double* __restrict__ v_t1, const R* __restrict__ dLdx_row, R* __restrict__ gF_row,
+                             int fmode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
   // element contributions are large and cancel at a vertex: summed in FP64
@@ -1350,9 +1368,13 @@ __global__ void k_adj_vertex(Dev<R> d, double* __restrict__ ax, double* __restri
   const double h = (double)d.h;
   st3(ax, i, V3<double>{a_x.x + (double)r1.x + (double)dl.x, a_x.y + (double)r1.y + (double)dl.y,
                         a_x.z + (double)r1.z + (double)dl.z});
-  st3(av, i, V3<double>{a_v.x + h * a_x.x + (double)r2.x, a_v.y + h * a_x.y + (double)r2.y,
-                        a_v.z + h * a_x.z + (double)r2.z});
-  if (gF_row && u >= 0) st3(gF_row, u, V3<R>{(R)(h * lam.x), (R)(h * lam.y), (R)(h * lam.z)});
+  const V3<double> nv = {a_v.x + h * a_x.x + (double)r2.x, a_v.y + h * a_x.y + (double)r2.y,
+                         a_v.z + h * a_x.z + (double)r2.z};
+  st3(av, i, nv);
+  if (gF_row && u >= 0) {
+    if (fmode == 0) st3(gF_row, u, V3<R>{(R)(h * lam.x), (R)(h * lam.y), (R)(h * lam.z)});
+    else st3(gF_row, u, d.pinned[i] ? V3<R>{R(0), R(0), R(0)} : V3<R>{(R)nv.x, (R)nv.y, (R)nv.z});
+  }
   const V3<double> vt = ld3(v_t, i), vt1 = ld3(v_t1, i);
   const double m1 = (double)d.area3[i];
   d.row_sc[i] = m1 * ((double)lam.x * ((double)d.h * (double)d.gx - (vt1.x - vt.x)) +

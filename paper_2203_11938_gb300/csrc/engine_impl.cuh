@@ -171,6 +171,7 @@ class Engine final : public EngineBase {
     tmp_xd_ = alloc<double>(n3, &rc);
     tmp_vd_ = alloc<double>(n3, &rc);
     tmp_ud_ = alloc<double>(n3, &rc);
+    vin_ = alloc<double>(n3, &rc);
     mat_ = alloc<R>(4 * (size_t)L_.S, &rc);
     mat_tmp_ = alloc<R>(4 * (size_t)L_.S, &rc);
     d.material = mat_;
@@ -190,17 +191,22 @@ class Engine final : public EngineBase {
       *err = "CUDA setup failed";
       return CLOTH_ERR_CUDA;
     }
-    // CG kernels: as many CTAs as can be resident at once, each looping over work entries
-    int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
+    // CG kernels of the resident-grid schedules: as many CTAs as can be resident at once
+    // (each kernel by its own occupancy), each looping over work entries
+    int dev = 0, sms = 0, per_sm = 0, per_sm_f = 0, per_sm2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R, false>, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_cg_spmv<R, true>, kThreads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_update<R>, kThreads, 0) != cudaSuccess) {
       *err = "CUDA occupancy query failed";
       return CLOTH_ERR_CUDA;
     }
-    cg_grid_ = std::max(1, std::min(d.NW, sms * std::max(1, std::min(per_sm, per_sm2))));
-    resident_grid_ = cg_grid_;
+    auto resident = [&](int per) { return std::max(1, std::min(d.NW, sms * std::max(1, per))); };
+    res_spmv_[0] = resident(per_sm);
+    res_spmv_[1] = resident(per_sm_f);
+    res_upd_ = resident(per_sm2);
+    spmv_grid_ = upd_grid_ = d.NW;
     // per-sheet cluster solver: every sheet of at most 8 x 4 work entries (8192 rows) gets a
     // cluster of CL CTAs with EPC entries each, CL * EPC >= its entries; sheets of a class
     // (CL, EPC) are listed largest first, so the longest solves start first
@@ -373,10 +379,10 @@ class Engine final : public EngineBase {
     auto one = [&]() {
       switch (which) {
         case 0:
-          if (sched_fused_) k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, st>>>(d_);
-          else k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, st>>>(d_);
+          if (sched_fused_) k_cg_spmv<R, true><<<spmv_grid_, kThreads, 0, st>>>(d_);
+          else k_cg_spmv<R, false><<<spmv_grid_, kThreads, 0, st>>>(d_);
           break;
-        case 1: k_cg_update<R><<<cg_grid_, kThreads, 0, st>>>(d_); break;
+        case 1: k_cg_update<R><<<upd_grid_, kThreads, 0, st>>>(d_); break;
         case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr); break;
         case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
         default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
@@ -568,8 +574,9 @@ class Engine final : public EngineBase {
   int assemble_at(const void* x, const void* v, const void* F, cudaStream_t st) {
     gather_state((const R*)x, tmp_xd_, st);
     gather_state((const R*)v, tmp_vd_, st);
-    elements(tmp_xd_, tmp_vd_, st);
-    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, (const R*)F);
+    const double* vs = start_velocity(tmp_vd_, (const R*)F, st);
+    elements(tmp_xd_, vs, st);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, o_.force_mode == CLOTH_FORCES_VELOCITY ? nullptr : (const R*)F);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -580,7 +587,8 @@ class Engine final : public EngineBase {
   void set_schedule(int sched) {
     schedule_ = sched & 7;
     sched_fused_ = (schedule_ & 2) != 0;
-    cg_grid_ = (schedule_ & 1) ? resident_grid_ : d_.NW;
+    spmv_grid_ = (schedule_ & 1) ? res_spmv_[sched_fused_ ? 1 : 0] : d_.NW;
+    upd_grid_ = (schedule_ & 1) ? res_upd_ : d_.NW;
     // bit 2: every sheet is solved by the per-sheet cluster solver (the device loop
     // hands over at once)
     d_.tail_threshold = ((schedule_ & 4) && sheet_solver_ok_) ? std::min(L_.S, handover_) : 0;
@@ -589,12 +597,12 @@ class Engine final : public EngineBase {
   int scalar_grid() const { return (L_.S * 32 + 255) / 256; }
 
   void emit_cg_body(cudaStream_t s, int phase, cudaGraphConditionalHandle cond, int use_cond) {
-    if (sched_fused_) k_cg_spmv<R, true><<<cg_grid_, kThreads, 0, s>>>(d_);
-    else k_cg_spmv<R, false><<<cg_grid_, kThreads, 0, s>>>(d_);
+    if (sched_fused_) k_cg_spmv<R, true><<<spmv_grid_, kThreads, 0, s>>>(d_);
+    else k_cg_spmv<R, false><<<spmv_grid_, kThreads, 0, s>>>(d_);
     k_cg_scalar_alpha<R><<<scalar_grid(), 256, 0, s>>>(d_, phase, cond, use_cond);
-    k_cg_update<R><<<cg_grid_, kThreads, 0, s>>>(d_);
+    k_cg_update<R><<<upd_grid_, kThreads, 0, s>>>(d_);
     k_cg_scalar_beta<R><<<scalar_grid(), 256, 0, s>>>(d_, phase, cond, use_cond);
-    if (!sched_fused_) k_cg_dir<R><<<cg_grid_, kThreads, 0, s>>>(d_);
+    if (!sched_fused_) k_cg_dir<R><<<upd_grid_, kThreads, 0, s>>>(d_);
   }
 
   static std::string tune_cache_path() {
@@ -684,7 +692,7 @@ class Engine final : public EngineBase {
       for (int sched = 0; sched < 4; ++sched) {
         set_schedule(sched);
         k_solve_begin<R><<<1, 32, 0, st>>>(d_);
-        k_cg_init<R><<<cg_grid_, kThreads, 0, st>>>(d_, d_.bvec);
+        k_cg_init<R><<<upd_grid_, kThreads, 0, st>>>(d_, d_.bvec);
         k_cg_scalar_init<R><<<scalar_grid(), 256, 0, st>>>(d_, kPhaseForward);
         emit_cg_body(st, kPhaseForward, 0, 0);  // warm-up
         CLOTH_CUDA(cudaEventRecord(ev0_, st));
@@ -773,7 +781,7 @@ class Engine final : public EngineBase {
   // conditional WHILE node whose condition the kernels clear when the last sheet ends.
   int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
     launch(k_solve_begin<R>, dim3(1), dim3(32), st, d_);
-    launch(k_cg_init<R>, dim3(cg_grid_), dim3(kThreads), st, d_, rhs);
+    launch(k_cg_init<R>, dim3(upd_grid_), dim3(kThreads), st, d_, rhs);
     launch(k_cg_scalar_init<R>, dim3(scalar_grid()), dim3(256), st, d_, phase);
     CLOTH_CUDA(cudaGetLastError());
     if (capturing) {
@@ -859,9 +867,19 @@ class Engine final : public EngineBase {
     return CLOTH_OK;
   }
 
-  // One implicit step from (x, v) to (xn, vn); F: user-layout force row or null.
-  int step(const double* x, const double* v, const R* F, double* xn, double* vn, R* traj_row, int phase,
+  // The velocity a step starts from: v, or v + F_t with velocity-increment forces.
+  const double* start_velocity(const double* v, const R* F, cudaStream_t st) {
+    if (o_.force_mode != CLOTH_FORCES_VELOCITY || !F) return v;
+    launch(k_add_increment<R>, dim3(grid_rows()), dim3(256), st, d_, v, F, vin_);
+    return vin_;
+  }
+
+  // One implicit step from (x, v) to (xn, vn); F: user-layout force row (or velocity
+  // increments, by the force mode) or null.
+  int step(const double* x, const double* v0, const R* F, double* xn, double* vn, R* traj_row, int phase,
            cudaStream_t st, bool cap) {
+    const double* v = start_velocity(v0, F, st);
+    if (o_.force_mode == CLOTH_FORCES_VELOCITY) F = nullptr;
     elements(x, v, st);
     launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, F);
     CLOTH_CUDA(cudaGetLastError());
@@ -937,8 +955,9 @@ class Engine final : public EngineBase {
         if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         if (L_.E) launch(k_adj_hinge<R>, dim3(ge), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         R* gF = g_forces ? (R*)g_forces + (size_t)t * nu3 : nullptr;
-        launch(k_adj_vertex<R>, dim3(grid_rows()), dim3(256), st, d_, ax_, av_, (const double*)sv(j), (const double*)sv(j + 1),
-               (const R*)dL_dx + (size_t)t * nu3, gF);
+        const double* vstart = start_velocity(sv(j), force_row(fwd_forces_, t), st);
+        launch(k_adj_vertex<R>, dim3(grid_rows()), dim3(256), st, d_, ax_, av_, vstart, (const double*)sv(j + 1),
+               (const R*)dL_dx + (size_t)t * nu3, gF, (int)o_.force_mode);
         launch(k_param_acc<R>, dim3(L_.S), dim3(kThreads), st, d_);
         CLOTH_CUDA(cudaGetLastError());
       }
@@ -998,6 +1017,7 @@ class Engine final : public EngineBase {
   bool have_forward_ = false;
   double *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;
   double *tmp_xd_ = nullptr, *tmp_vd_ = nullptr, *tmp_ud_ = nullptr;
+  double* vin_ = nullptr;  // a step's starting velocity v_t + F_t (velocity-increment forces)
   double *ax_ = nullptr, *av_ = nullptr;
   R *tmp_a_ = nullptr, *tmp_b_ = nullptr;
   R *mat_ = nullptr, *mat_tmp_ = nullptr;
@@ -1006,13 +1026,13 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;
   std::vector<CachedGraph> graphs_;
   int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
-  int cg_grid_ = 1;       // CTAs of the CG kernels (the schedule's choice)
+  int spmv_grid_ = 1, upd_grid_ = 1;  // CTAs of the SpMV and of the other CG row kernels
   std::vector<SheetClass> classes_;  // size classes of the per-sheet cluster solver
   const int* sheet_lists_ = nullptr;  // their sheets, class after class
   bool sheet_solver_ok_ = false;      // every sheet fits one cluster
   int handover_ = 1 << 30;            // sheets left when the device loop hands over
   cudaEvent_t fork_ev_ = nullptr;
-  int resident_grid_ = 1; // CTAs resident at once on the whole GPU
+  int res_spmv_[2] = {1, 1}, res_upd_ = 1;  // CTAs resident at once (SpMV separate / fused, update)
   bool sched_fused_ = true;
   int schedule_ = 3;
   cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;

@@ -51,6 +51,7 @@ class ClothOpts(ctypes.Structure):
         ("precond", ctypes.c_int32),
         ("cg_schedule", ctypes.c_int32),
         ("cg_handover", ctypes.c_int32),
+        ("force_mode", ctypes.c_int32),
     ]
 
 
@@ -150,7 +151,7 @@ class ClothBatch:
 
     def __init__(self, meshes, *, steps, dt, precision="f32", cg_tol=1e-6, cg_max_iter=2000, checkpoint_every=0,
                  gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16, precond="block",
-                 cg_schedule=-1, cg_handover=0):
+                 cg_schedule=-1, cg_handover=0, force_mode="force"):
         import torch
 
         if not torch.cuda.is_available():
@@ -172,6 +173,7 @@ class ClothBatch:
         o.precond = 1 if precond == "block" else 0
         o.cg_schedule = int(cg_schedule)
         o.cg_handover = int(cg_handover)
+        o.force_mode = {"force": 0, "velocity": 1}[force_mode]
         self.opts = o
         self.steps = int(steps)
         self.dtype = torch.float64 if precision == "f64" else torch.float32

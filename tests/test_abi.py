@@ -41,7 +41,7 @@ def test_opts_struct_layout_matches_header(lib):
     assert o.precision == sim.FP32 and o.steps == 1 and o.cg_max_iter == 2000
     assert o.gravity[2] == pytest.approx(-9.8) and o.clamp_eta == pytest.approx(1e-3)
     assert o.exec == sim.EXEC_GRAPH and o.cg_poll_every == 16 and o.precond == 1 and o.cg_schedule == -1
-    assert o.cg_handover == 0
+    assert o.cg_handover == 0 and o.force_mode == 0
 
 
 def test_mesh_create_counts(lib):
@@ -81,7 +81,8 @@ def test_batch_create_rejects_bad_options_on_host(lib):
     h = ctypes.c_void_p()
     for field, value in (("steps", 0), ("dt", -1.0), ("cg_max_iter", 0), ("precision", 7), ("exec", 9),
                          ("clamp_eta", -1.0), ("cg_poll_every", 0), ("precond", 5),
-                         ("cg_schedule", 8), ("cg_schedule", -2), ("cg_handover", -1)):
+                         ("cg_schedule", 8), ("cg_schedule", -2), ("cg_handover", -1),
+                         ("force_mode", 2)):
         o = sim.default_opts()
         setattr(o, field, value)
         rc = lib.cloth_batch_create(arr, 1, ctypes.byref(o), ctypes.byref(h))
