@@ -888,7 +888,7 @@ __device__ __forceinline__ const R* pbuf(const Dev<R>& d, int parity) {
 
 // Ap = A p_k over all active sheets; warp partials of p.Ap.
 template <class R, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_cg_spmv(Dev<R> d) {
+__global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
   const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
     const int s = d.work_sheet[w];
