@@ -328,7 +328,7 @@ __device__ __forceinline__ void finish_sheet(const Dev<R>& d, int s, int phase, 
   si[1] += (unsigned)d.cg[s].iters;
   const int left = atomicSub(d.active, 1) - 1;
   // exactly one thread sees each value of `left`: the one reaching the hand-over point
-  // ends the device loop (the cluster tail solver finishes the remaining sheets)
+  // ends the device loop (the per-sheet cluster solver finishes the remaining sheets)
   if (left == d.tail_threshold && use_cond) cudaGraphSetConditional(cond, 0);
 }
 
