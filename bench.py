@@ -335,14 +335,18 @@ def run_ours(args):
     one_step()
     torch.cuda.synchronize()
     mi = b.matrix_info()
-    es = 4 if dtype == torch.float32 else 8
-    # per block 9 values + 1 column index; per row: fused schedule (bit 1) reads z_k and
-    # p_{k-1} and writes p_k and Ap, else reads p_k and writes Ap (neighbour gathers hit L1/L2)
-    fused = bool(mi["cg_schedule"] & 2)
-    alg_bytes = mi["blocks"] * (9 * es + 4) + mi["rows"] * ((4 if fused else 2) * 3 * es)
-    spmv_ms = b.time_kernel("spmv", reps=50)
-    upd_ms = b.time_kernel("cg_update", reps=50)
     peak, peak_kind = measured_peak()
+    # every kernel cloth_time_kernel times: average of back-to-back full launches (CUDA
+    # events on the launching stream) against its algorithmic bytes (cloth_kernel_bytes)
+    kernels = {}
+    for name in ("spmv", "cg_update", "assemble", "elem_tri", "elem_hinge"):
+        ms_k = b.time_kernel(name, reps=50 if name in ("spmv", "cg_update") else 10)
+        by = b.kernel_bytes(name)
+        gbs = by / (ms_k / 1e3) / 1e9
+        kernels[name] = {"avg_launch_ms": round(ms_k, 5), "algorithmic_bytes": int(by), "GBps": round(gbs, 1),
+                         "frac_of_hbm_peak": round(gbs / peak, 4)}
+    spmv_ms = kernels["spmv"]["avg_launch_ms"]
+    alg_bytes = kernels["spmv"]["algorithmic_bytes"]
     achieved = alg_bytes / (spmv_ms / 1e3) / 1e9
     traffic = committed_traffic()
     roofline = {"bound": "hbm", "kernel": "k_cg_spmv (3x3-block SELL-32 difference-form SpMV, per-warp p.Ap partials)",
@@ -350,12 +354,7 @@ def run_ours(args):
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(spmv_ms, 5),
-                "bytes_per_vertex": round(alg_bytes / mi["rows"], 1),
-                "cg_update_ms": round(upd_ms, 5),
-                # update: p, Ap, r, z (3 es each), the solution dv read+write (FP64, or float-float
-                # hi + lo in FP32 mode: 24 B each way), r write, 3x3 inverse (9 es)
-                "cg_update_GBps": round(mi["rows"] * (3 * es * 5 + 9 * es + 48) / (upd_ms / 1e3) / 1e9, 1)}
-
+                "bytes_per_vertex": round(alg_bytes / mi["rows"], 1)}
     log(f"roofline {roofline}")
     # -------------------- plain single-sheet GPU path on a subset of the sheets
     plain = None
@@ -398,7 +397,7 @@ def run_ours(args):
             "config": dict(workload_config(wl, args.workload),
                            **{"l2": f"working set {b.workspace_bytes / 1e9:.2f} GB > 129 MB L2 (inputs larger than L2)",
                               "exec": args.exec_mode}),
-            "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps), "roofline": roofline,
+            "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps), "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "clocks": clocks,
             "cg_iters_per_step": {"forward": stats["fwd_cg_iters"] / (wl.steps * len(wl.sheets)),
                                   "adjoint": stats["bwd_cg_iters"] / (wl.steps * len(wl.sheets)),

@@ -210,6 +210,13 @@ int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks,
 int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* avg_ms,
                       void* stream);
 
+/* Algorithmic bytes of one launch of the kernel cloth_time_kernel times under the same
+ * id (compulsory traffic: every input the kernel needs and every output it writes,
+ * once; vertex state read once per vertex), for the roofline of that kernel: the SpMV
+ * counts the nonzero blocks (9 values + column each) and its vector traffic for the
+ * schedule in use.  No device work; error INVALID_ARG for another id. */
+int cloth_kernel_bytes(cloth_batch* batch, int32_t kernel, int64_t* bytes);
+
 /* ---- single-kernel entry points (parity checks of each stage) ---- */
 
 /* Internal elastic forces f = -dE/dx at positions x (device [N_total][3]):

@@ -176,6 +176,11 @@ int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks, 
   return batch->engine->matrix_info(rows, blocks, stored_blocks, cg_schedule);
 }
 
+int cloth_kernel_bytes(cloth_batch* batch, int32_t kernel, int64_t* bytes) {
+  CLOTH_NEED_BATCH("cloth_kernel_bytes");
+  return batch->engine->kernel_bytes(kernel, bytes);
+}
+
 int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* avg_ms, void* stream) {
   CLOTH_NEED_BATCH("cloth_time_kernel");
   return batch->engine->time_kernel(kernel, reps, avg_ms, stream);

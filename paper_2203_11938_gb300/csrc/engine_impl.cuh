@@ -353,17 +353,54 @@ class Engine final : public EngineBase {
     return CLOTH_OK;
   }
 
+  int64_t nonzero_blocks() const {
+    int64_t nb = 0;
+    for (size_t i = 0; i + 1 < L_.contrib_ptr.size(); ++i) nb += L_.contrib_ptr[i + 1] > L_.contrib_ptr[i] ? 1 : 0;
+    // rows without element blocks (padding) still hold their identity diagonal
+    for (int i = 0; i < L_.Np; ++i) nb += L_.i2u[i] < 0 ? 1 : 0;
+    return nb;
+  }
+
   int matrix_info(int64_t* rows, int64_t* blocks, int64_t* slots, int32_t* schedule) override {
     if (schedule) *schedule = schedule_;
     if (rows) *rows = L_.Np;
-    if (blocks) {
-      int64_t nb = 0;
-      for (size_t i = 0; i + 1 < L_.contrib_ptr.size(); ++i) nb += L_.contrib_ptr[i + 1] > L_.contrib_ptr[i] ? 1 : 0;
-      // rows without element blocks (padding) still hold their identity diagonal
-      for (int i = 0; i < L_.Np; ++i) nb += L_.i2u[i] < 0 ? 1 : 0;
-      *blocks = nb;
-    }
+    if (blocks) *blocks = nonzero_blocks();
     if (slots) *slots = (int64_t)L_.total_slots() * 32;
+    return CLOTH_OK;
+  }
+
+  // Algorithmic (compulsory) bytes of one launch of a kernel cloth_time_kernel times:
+  // every input the kernel needs and every output it writes, once.
+  int kernel_bytes(int which, int64_t* out) override {
+    if (!out) return invalid("cloth_kernel_bytes: null output");
+    const int64_t es = sizeof(R), rows = L_.Np, M = L_.M, E = L_.E;
+    const int64_t stored = (int64_t)L_.total_slots() * 32;
+    switch (which) {
+      case 0:  // 3x3 values + column per nonzero block; z, p_{k-1} read and p_k, Ap written
+               // (fused) or p_k read and Ap written
+        *out = nonzero_blocks() * (9 * es + 4) + rows * (sched_fused_ ? 4 : 2) * 3 * es;
+        break;
+      case 1:  // p, Ap, r read; r, z written; 3x3 inverse; the solution read and written (24 B each)
+        *out = rows * (5 * 3 * es + 9 * es + 48);
+        break;
+      case 2:  // per row: pin flag, mass area, two index words, b and the 3x3 inverse written;
+               // per force contribution: index + 3 doubles; per stored block: column, pin flag
+               // of the column, contributor range, 9 values written; per contribution: index +
+               // the element's 3x3 block
+        *out = rows * (1 + es + 8 + 12 * es) + (int64_t)L_.vf.size() * 28 + stored * (9 + 9 * es) +
+               (int64_t)L_.contrib.size() * (4 + 9 * es);
+        break;
+      case 3:  // per triangle: 3 vertex ids, sheet id, rest data (batch precision and FP64),
+               // rest metric, FP64 force vector and 6 Hessian blocks written; x, v once per row
+        *out = M * (16 + 5 * es + 40 + 24 + 72 + 54 * es) + rows * 48;
+        break;
+      case 4:  // per hinge: 4 vertex ids, sheet id, rest data (both precisions), FP64 force
+               // vector and 10 Hessian blocks written; x, v once per row
+        *out = E * (20 + 2 * es + 16 + 96 + 90 * es) + rows * 48;
+        break;
+      default:
+        return invalid("cloth_kernel_bytes: kernel must be 0..4");
+    }
     return CLOTH_OK;
   }
 

@@ -32,7 +32,7 @@ EXPORTS = (
     "cloth_batch_destroy", "cloth_batch_info", "cloth_forward", "cloth_backward", "cloth_loss_l2",
     "cloth_loss_pinhole", "cloth_stats", "cloth_internal_forces", "cloth_system_dense", "cloth_spmv",
     "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel", "cloth_loss_l2_static",
-    "cloth_sheet_iterations",
+    "cloth_sheet_iterations", "cloth_kernel_bytes",
 )
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_stats.argtypes = [_vp] * 5
     lib.cloth_matrix_info.argtypes = [_vp] * 5
     lib.cloth_sheet_iterations.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+    lib.cloth_kernel_bytes.argtypes = [_vp, ctypes.c_int32, _vp]
     lib.cloth_time_kernel.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.cloth_internal_forces.argtypes = [_vp] * 6
     lib.cloth_system_dense.argtypes = [_vp] * 8
@@ -309,6 +310,12 @@ class ClothBatch:
         _check(_lib.cloth_time_kernel(self._h, self.KERNELS[name], int(reps), ctypes.byref(ms), self._stream()),
                "cloth_time_kernel")
         return ms.value
+
+    def kernel_bytes(self, name):
+        """Algorithmic bytes of one launch of the kernel time_kernel(name) times."""
+        b = ctypes.c_int64()
+        _check(_lib.cloth_kernel_bytes(self._h, self.KERNELS[name], ctypes.byref(b)), "cloth_kernel_bytes")
+        return b.value
 
     def internal_forces(self, material, x):
         N, S = self.total_vertices, self.count
