@@ -103,8 +103,8 @@ typedef struct cloth_opts {
                                acts: CLOTH_FORCES_FORCE (a force [N] added to f, Eq. 3)
                                or CLOTH_FORCES_VELOCITY (a velocity increment [m/s]
                                added to the free vertices' velocities before step t,
-                               the form the paper's corrective forces take in its
-                               experiments, Sec. 4); the backward then returns dL/dF_t
+                               the form the paper's implementation details give its
+                               corrective forces, Sec. 3.4); the backward then returns dL/dF_t
                                in the same sense                                      */
 } cloth_opts;
 

@@ -695,7 +695,8 @@ void oracle_system_matvec(void* h, const double* material, double eta, double dt
 // Forward trajectory.  x0, v0: [n][3]; forces: [steps][n][3] or NULL;
 // force_mode 0: F_t is a force [N] added to f (Eq. 3); 1: F_t is a velocity increment
 // [m/s] added to the free vertices' velocities before step t (the corrective forces'
-// form in the paper's experiments), v'_t = v_t + F_t, and the step runs from (x_t, v'_t).
+// form in the paper's implementation details, Sec. 3.4), v'_t = v_t + F_t, and the step
+// runs from (x_t, v'_t).
 // traj_x, traj_v: [steps+1][n][3] (traj_v holds v_t, before any increment); cg_iters [steps];
 // status: worst per-step solver status (0 ok, 1 maxiter, 2 indefinite, 3 non-finite).
 int oracle_forward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,

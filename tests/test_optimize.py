@@ -1,0 +1,72 @@
+"""The optimiser driver: the adaptive temporal window's schedule on the host (CPU), and
+one small optimisation through the CUDA library (GPU)."""
+import numpy as np
+import pytest
+
+from paper_2203_11938_gb300.optimize import AdaptiveWindow
+
+
+def test_window_first_growth_at_the_cap_sets_threshold_from_frame_5():
+    w = AdaptiveWindow(total=10, first=5, max_iters=3)
+    e = np.arange(11, dtype=float) + 1.0  # frame t has energy t + 1 (frame 5: 6.0)
+    grew = [w.step(e) for _ in range(3)]
+    assert grew == [False, False, True]
+    assert w.active == 6 and w.threshold == 6.0 and w.iters == 0
+
+
+def test_window_grows_when_the_latest_frame_drops_below_threshold():
+    w = AdaptiveWindow(total=10, first=5, max_iters=4)
+    e = np.full(11, 2.0)
+    for _ in range(4):
+        w.step(e)
+    assert w.active == 6 and w.threshold == 2.0
+    e[6] = 1.5  # below b: the next frame joins at once
+    assert w.step(e) and w.active == 7
+    e[7] = 2.5  # above b: only the cap makes it grow
+    assert [w.step(e) for _ in range(4)] == [False, False, False, True]
+    assert w.active == 8
+
+
+def test_window_stops_at_the_last_frame():
+    w = AdaptiveWindow(total=6, first=5, max_iters=1)
+    e = np.zeros(7)
+    assert w.step(e) and w.active == 6 and w.done
+    assert not w.step(e) and w.active == 6
+
+
+def test_window_shorter_than_first():
+    w = AdaptiveWindow(total=3, first=5, max_iters=2)
+    assert w.active == 3 and w.done
+
+
+@pytest.mark.gpu
+def test_fit_recovers_material_from_tracks():
+    """6x6 sheet, 10 steps, FP64: tracks of a ground-truth material; Adam (lr 2e-2, log
+    parameters) from a perturbed material, with the adaptive window, grows the window
+    and at least halves the reprojection energy of all frames.  Under gravity alone the
+    trajectory depends on Y / rho and k_b / rho only (gravity and inertia both scale with
+    rho), so the single parameters are not identifiable from tracks and are not checked."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11938_gb300 import sim, workloads as W
+    from paper_2203_11938_gb300.optimize import fit, frame_energies, project
+
+    N, T, dt = 6, 10, 1.0 / 30.0
+    rest, tris = W.grid_mesh(N)
+    b = sim.ClothBatch([(rest, tris, W.pins(N, "top2"))], steps=T, dt=dt, precision="f64", cg_tol=1e-10,
+                       cg_max_iter=5000)
+    cam = (500.0, 0.5, 0.5, 2.0)
+    truth = torch.tensor([[2.0e3, 0.3, 5e-4, 0.15]], dtype=torch.float64, device="cuda")
+    x0 = torch.as_tensor(rest, dtype=torch.float64, device="cuda")
+    v0 = torch.zeros_like(x0)
+    traj, st = b.forward(truth, x0, v0)
+    tracks = project(traj, cam).contiguous()
+    start = truth * torch.tensor([1.4, 1.0, 0.6, 1.3], dtype=torch.float64, device="cuda")
+    e0 = frame_energies(b.forward(start, x0, v0)[0], tracks, cam)[1:].sum().item()
+    r = fit(b, start, x0, v0, tracks, cam, iters=40, lr=2e-2, first=5, max_iters=4, optimise_forces=False)
+    assert r.window.active > 5
+    mfit = torch.as_tensor(r.material, device="cuda")
+    e1 = frame_energies(b.forward(mfit.contiguous(), x0, v0)[0], tracks, cam)[1:].sum().item()
+    assert e1 < 0.5 * e0
+    assert r.history[-1][0] == r.window.active or r.history[-1][0] + 1 == r.window.active
