@@ -70,3 +70,64 @@ def test_fit_recovers_material_from_tracks():
     e1 = frame_energies(b.forward(mfit.contiguous(), x0, v0)[0], tracks, cam)[1:].sum().item()
     assert e1 < 0.5 * e0
     assert r.history[-1][0] == r.window.active or r.history[-1][0] + 1 == r.window.active
+
+
+class _FakeBatch:
+    """A stand-in with the ClothBatch call surface: x_t = x0 + t * (Y/1000, kb*1e4, rho) per
+    vertex; records the loss gradient handed to backward."""
+
+    def __init__(self, torch, T, n):
+        self.torch, self.steps, self.n, self.seen = torch, T, n, []
+
+    def forward(self, mat, x0, v0, F):
+        t = self.torch.arange(self.steps + 1, dtype=x0.dtype)[:, None, None]
+        rate = self.torch.stack([mat[0, 0] / 1000, mat[0, 2] * 1e4, mat[0, 3]])
+        self.rate = rate
+        return x0[None] + t * rate[None, None, :], self.torch.zeros(1, dtype=self.torch.int32)
+
+    def loss_pinhole(self, traj, tracks, camera):
+        from paper_2203_11938_gb300.optimize import project
+
+        tr = traj.clone().requires_grad_(True)
+        d = project(tr, camera) - tracks
+        L = (d[1:] * d[1:]).sum()
+        (g,) = self.torch.autograd.grad(L, tr)
+        return L.detach()[None], g
+
+    def backward(self, dL):
+        self.seen.append(dL.clone())
+        t = self.torch.arange(self.steps + 1, dtype=dL.dtype)[:, None]
+        dr = (dL * t[:, :, None]).sum(dim=(0, 1))  # dL/d rate
+        gm = self.torch.zeros(1, 4, dtype=dL.dtype)
+        gm[0, 0], gm[0, 2], gm[0, 3] = dr[0] / 1000, dr[1] * 1e4, dr[2]
+        return {"material": gm, "forces": self.torch.zeros(self.steps, self.n, 3, dtype=dL.dtype),
+                "status": self.torch.zeros(1, dtype=self.torch.int32)}
+
+
+def test_fit_masks_inactive_frames_and_steps_log_parameters():
+    """Host plumbing of fit() on a fake batch: frames after the active one reach the
+    backward with zero gradient, and the first Adam step moves each log-parameter by
+    -lr * sign(dL/dlog p) = -lr * sign(p * dL/dp)."""
+    torch = pytest.importorskip("torch")
+    from paper_2203_11938_gb300.optimize import fit, project
+
+    T, n = 8, 4
+    b = _FakeBatch(torch, T, n)
+    x0 = torch.tensor([[0.1, 0.2, 0.0], [0.4, 0.1, 0.0], [0.3, 0.5, 0.0], [0.7, 0.6, 0.0]], dtype=torch.float64)
+    cam = (500.0, 0.5, 0.5, 2.0)
+    truth = torch.tensor([[1.0e3, 0.3, 1e-4, 0.1]], dtype=torch.float64)
+    traj, _ = b.forward(truth, x0, None, None)
+    tracks = project(traj, cam)
+    start = truth * torch.tensor([1.2, 1.0, 0.8, 1.1], dtype=torch.float64)
+    lr = 1e-3
+    r = fit(b, start, x0, torch.zeros_like(x0), tracks, cam, iters=1, lr=lr, first=5, max_iters=10,
+            optimise_forces=False)
+    dL = b.seen[0]
+    assert torch.all(dL[6:] == 0) and torch.any(dL[1:6] != 0)
+    # expected gradient of log p at the start, from the unmasked frames
+    t = torch.arange(T + 1, dtype=torch.float64)[:, None]
+    dr = (dL * t[:, :, None]).sum(dim=(0, 1))
+    g = torch.stack([dr[0] / 1000 * start[0, 0], dr[1] * 1e4 * start[0, 2], dr[2] * start[0, 3]])
+    moved = np.log(r.material[0, [0, 2, 3]]) - np.log(start[0, [0, 2, 3]].numpy())
+    np.testing.assert_allclose(moved, -lr * np.sign(g.numpy()), rtol=1e-6)
+    assert r.material[0, 1] == pytest.approx(0.3)
