@@ -61,10 +61,12 @@ def _load():
         lib.oracle_system_matvec.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp,
                                              _dp, _dp, _dp, _dp]
         lib.oracle_forward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                       ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, _dp, _dp, _ip, _ip]
+                                       ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                       _ip, _ip]
         lib.oracle_forward.restype = ctypes.c_int
         lib.oracle_backward.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                        ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _ip]
+                                        ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                        _dp, _dp, _dp, _dp, _ip, _ip]
         lib.oracle_backward.restype = ctypes.c_int
         lib.oracle_loss_l2.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
         lib.oracle_loss_l2.restype = ctypes.c_double
@@ -163,9 +165,10 @@ class OracleSim:
 
     # -- trajectory
     def forward(self, material, x0, v0, forces, *, dt, steps, tol, max_iter, gravity, eta=ETA, precond=PRECOND,
-                force_mode=0):
+                force_mode=0, air_density=0.0, wind=None):
         """force_mode 0: forces [N] added to f; 1: velocity increments [m/s] added to the
-        free vertices' velocities before each step."""
+        free vertices' velocities before each step.  air_density > 0 with wind (3,):
+        quadratic air drag of the relative wind on every free vertex."""
         tx = np.zeros((steps + 1, self.n, 3))
         tv = np.zeros((steps + 1, self.n, 3))
         iters = np.zeros(steps, np.int32)
@@ -173,12 +176,15 @@ class OracleSim:
         Fp = None if forces is None else _f64(forces, (steps, self.n, 3))
         self._lib.oracle_forward(self._h, _d(_f64(material)), float(eta), int(precond), float(dt), int(steps), float(tol), int(max_iter),
                                  _d(_f64(gravity)), _d(_f64(x0, (self.n, 3))), _d(_f64(v0, (self.n, 3))), _d(Fp),
-                                 int(force_mode), _d(tx), _d(tv), iters.ctypes.data_as(_ip), ctypes.byref(st))
+                                 int(force_mode), float(air_density), _d(None if wind is None else _f64(wind)),
+                                 _d(tx), _d(tv), iters.ctypes.data_as(_ip), ctypes.byref(st))
         return tx, tv, iters, st.value
 
     def backward(self, material, traj_x, traj_v, dL_dx, *, dt, steps, tol, max_iter, gravity, eta=ETA,
-                 precond=PRECOND, forces=None, force_mode=0):
-        """forces, force_mode: as given to forward (the forces are read in mode 1 only)."""
+                 precond=PRECOND, forces=None, force_mode=0, air_density=0.0, wind=None):
+        """forces, force_mode, air_density, wind: as given to forward (the forces are read
+        in mode 1 only).  The result adds "wind" = dL/dw."""
+        gw = np.zeros(3)
         Fp = None if forces is None else _f64(forces, (steps, self.n, 3))
         gm = np.zeros(4)
         gF = np.zeros((steps, self.n, 3))
@@ -188,9 +194,9 @@ class OracleSim:
         st = ctypes.c_int(0)
         self._lib.oracle_backward(self._h, _d(_f64(material)), float(eta), int(precond), float(dt), int(steps), float(tol), int(max_iter),
                                   _d(_f64(gravity)), _d(_f64(traj_x)), _d(_f64(traj_v)), _d(Fp), int(force_mode),
-                                  _d(_f64(dL_dx)),
-                                  _d(gm), _d(gF), _d(gx0), _d(gv0), iters.ctypes.data_as(_ip), ctypes.byref(st))
-        return dict(material=gm, forces=gF, x0=gx0, v0=gv0, cg_iters=iters, status=st.value)
+                                  float(air_density), _d(None if wind is None else _f64(wind)), _d(_f64(dL_dx)),
+                                  _d(gm), _d(gF), _d(gx0), _d(gv0), _d(gw), iters.ctypes.data_as(_ip), ctypes.byref(st))
+        return dict(material=gm, forces=gF, x0=gx0, v0=gv0, wind=gw, cg_iters=iters, status=st.value)
 
 
 def membrane_element(rest, x, Y, nu):

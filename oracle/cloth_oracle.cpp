@@ -512,6 +512,33 @@ Sparse system_matrix(const Sim& s, const Mat& mt, double h, const Sparse& Hm, co
   return A;
 }
 
+// ------------------------------------------------------------------- air drag
+// Wind: the air moves at the sheet's wind velocity w (density rho_air).  Each free vertex
+// feels the quadratic drag of the relative air velocity d = w - v on its lumped rest area
+// A_i (the area that also lumps its mass):  f_i = rho_air A_i |d|_e d,  with the smooth
+// magnitude |d|_e = sqrt(d.d + e^2), e = kDragEps.  Its velocity Jacobian is
+// df/dv = -rho_air A_i G(d),  G(d) = |d|_e I + d d^T / |d|_e  (symmetric positive
+// definite), which enters the step matrix as + h rho_air A_i G (Eq. 5 with df/dv != 0).
+constexpr double kDragEps = 1e-3;
+
+double drag_norm(const double d[3]) { return std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + kDragEps * kDragEps); }
+
+void drag_G(const double d[3], double G[9]) {
+  const double n = drag_norm(d);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) G[3 * a + b] = (a == b ? n : 0.0) + d[a] * d[b] / n;
+}
+
+// out_k = a^T (dG/dd_k) b, k = 0..2 (the derivative of G(d) contracted with a and b)
+void drag_dG(const double d[3], const double a[3], const double b[3], double out[3]) {
+  const double n = drag_norm(d);
+  const double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+  const double ad = a[0] * d[0] + a[1] * d[1] + a[2] * d[2];
+  const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
+  for (int k = 0; k < 3; ++k)
+    out[k] = d[k] / n * ab + (a[k] * db + ad * b[k]) / n - ad * db * d[k] / (n * n * n);
+}
+
 }  // namespace
 
 // ============================================================== C interface
@@ -699,9 +726,11 @@ void oracle_system_matvec(void* h, const double* material, double eta, double dt
 // runs from (x_t, v'_t).
 // traj_x, traj_v: [steps+1][n][3] (traj_v holds v_t, before any increment); cg_iters [steps];
 // status: worst per-step solver status (0 ok, 1 maxiter, 2 indefinite, 3 non-finite).
+// air_density > 0 with wind (double[3]): the air drag above acts on every free vertex.
 int oracle_forward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,
                    int max_iter, const double* gravity, const double* x0, const double* v0, const double* forces,
-                   int force_mode, double* traj_x, double* traj_v, int* cg_iters, int* status) {
+                   int force_mode, double air_density, const double* wind, double* traj_x, double* traj_v,
+                   int* cg_iters, int* status) {
   const Sim* s = static_cast<Sim*>(h);
   Mat mt{material[0], material[1], material[2], material[3], eta, precond};
   const int N = 3 * s->n;
@@ -728,6 +757,18 @@ int oracle_forward(void* h, const double* material, double eta, int precond, dou
       b[i] = s->pinned[vi] ? 0.0 : dt * (f - dt * (Hv[i] + Hv2[i]));
     }
     Sparse A = system_matrix(*s, mt, dt, Hm, Hb);
+    if (air_density > 0.0 && wind)
+      for (int vi = 0; vi < s->n; ++vi) {
+        if (s->pinned[vi]) continue;
+        const double d[3] = {wind[0] - vv[3 * vi], wind[1] - vv[3 * vi + 1], wind[2] - vv[3 * vi + 2]};
+        const double c = air_density * s->area3[vi], n = drag_norm(d);
+        double G[9];
+        drag_G(d, G);
+        for (int a = 0; a < 3; ++a) {
+          b[3 * vi + a] += dt * c * n * d[a];
+          for (int q = 0; q < 3; ++q) A.add(3 * vi + a, 3 * vi + q, dt * c * G[3 * a + q]);
+        }
+      }
     int it = 0;
     int st = pcg(A, b, tol, max_iter, mt.precond, dv, &it);
     if (cg_iters) cg_iters[t] = it;
@@ -750,16 +791,20 @@ int oracle_forward(void* h, const double* material, double eta, int precond, dou
 // g_forces [steps][n][3], g_x0 [n][3], g_v0 [n][3]; cg_iters [steps]; status.
 // forces, force_mode: as given to oracle_forward (the forces are read only in mode 1,
 // where the step started from v'_t = v_t + F_t; then dL/dF_t = dL/dv'_t on free vertices).
+// air_density, wind: as given to oracle_forward; g_wind (double[3] or NULL): dL/dw.
 int oracle_backward(void* h, const double* material, double eta, int precond, double dt, int steps, double tol,
                     int max_iter, const double* gravity, const double* traj_x, const double* traj_v,
-                    const double* forces, int force_mode, const double* dL_dx, double* g_material,
-                    double* g_forces, double* g_x0, double* g_v0, int* cg_iters, int* status) {
+                    const double* forces, int force_mode, double air_density, const double* wind,
+                    const double* dL_dx, double* g_material, double* g_forces, double* g_x0, double* g_v0,
+                    double* g_wind, int* cg_iters, int* status) {
   const Sim* s = static_cast<Sim*>(h);
   Mat mt{material[0], material[1], material[2], material[3], eta, precond};
   const int N = 3 * s->n;
   std::vector<double> ax(dL_dx + (size_t)steps * N, dL_dx + (size_t)(steps + 1) * N), av(N, 0.0);
   std::vector<double> g(N), lam, Hl(N), Hl2(N), third(N), fm(N), fb(N), Hu(N), Hu2(N), u(N), dv(N);
-  double gY = 0.0, gkb = 0.0, grho = 0.0;
+  double gY = 0.0, gkb = 0.0, grho = 0.0, gw[3] = {0.0, 0.0, 0.0};
+  const bool drag = air_density > 0.0 && wind;
+  std::vector<double> vst(N);
   int worst = 0;
   for (int t = steps - 1; t >= 0; --t) {
     const double* x = traj_x + (size_t)t * N;
@@ -769,6 +814,7 @@ int oracle_backward(void* h, const double* material, double eta, int precond, do
     for (int i = 0; i < N; ++i) {
       u[i] = vn[i];
       const double vstart = v[i] + ((F && !s->pinned[i / 3]) ? F[i] : 0.0);  // v'_t
+      vst[i] = vstart;
       dv[i] = vn[i] - vstart;
       // adjoint of dv: v_{t+1} = v_t + dv and x_{t+1} = x_t + h v_{t+1}
       g[i] = s->pinned[i / 3] ? 0.0 : av[i] + dt * ax[i];
@@ -776,6 +822,15 @@ int oracle_backward(void* h, const double* material, double eta, int precond, do
     Sparse Hm(N), Hb(N);
     internal_hessian(*s, mt, x, Hm, Hb);
     Sparse A = system_matrix(*s, mt, dt, Hm, Hb);
+    if (drag)
+      for (int vi = 0; vi < s->n; ++vi) {
+        if (s->pinned[vi]) continue;
+        const double d[3] = {wind[0] - vst[3 * vi], wind[1] - vst[3 * vi + 1], wind[2] - vst[3 * vi + 2]};
+        double G[9];
+        drag_G(d, G);
+        for (int a = 0; a < 3; ++a)
+          for (int q = 0; q < 3; ++q) A.add(3 * vi + a, 3 * vi + q, dt * air_density * s->area3[vi] * G[3 * a + q]);
+      }
     int it = 0;
     int st = pcg(A, g, tol, max_iter, mt.precond, lam, &it);
     worst = std::max(worst, st);
@@ -811,8 +866,28 @@ int oracle_backward(void* h, const double* material, double eta, int precond, do
       grho += lam[i] * s->area3[i / 3] * (dt * gravity[i % 3] - dv[i]);
       ax[i] = ax[i] + dt * Kxlam - dt * dt * third[i] + dL_dx[(size_t)t * N + i];
       av[i] = vtot + dt * dt * Klam;  // adjoint of the step's starting velocity (= of v_t)
-      if (g_forces && force_mode == 1) g_forces[(size_t)t * N + i] = s->pinned[i / 3] ? 0.0 : av[i];
     }
+    // air drag: b depends on w and on the starting velocity through f = c |d|_e d, A
+    // through G(d); with q = h c (G lam - (dG/dd)[lam, dv]):  w_bar += q, v_bar -= q
+    if (drag)
+      for (int vi = 0; vi < s->n; ++vi) {
+        if (s->pinned[vi]) continue;
+        const double d[3] = {wind[0] - vst[3 * vi], wind[1] - vst[3 * vi + 1], wind[2] - vst[3 * vi + 2]};
+        const double c = air_density * s->area3[vi];
+        double G[9], T[3];
+        drag_G(d, G);
+        drag_dG(d, &lam[3 * vi], &dv[3 * vi], T);
+        for (int a = 0; a < 3; ++a) {
+          double Gl = 0.0;
+          for (int q = 0; q < 3; ++q) Gl += G[3 * a + q] * lam[3 * vi + q];
+          const double qa = dt * c * (Gl - T[a]);
+          gw[a] += qa;
+          av[3 * vi + a] -= qa;
+        }
+      }
+    if (g_forces && force_mode == 1)
+      for (int i = 0; i < N; ++i) g_forces[(size_t)t * N + i] = s->pinned[i / 3] ? 0.0 : av[i];
+
   }
   if (g_material) {
     g_material[0] = gY;
@@ -820,6 +895,8 @@ int oracle_backward(void* h, const double* material, double eta, int precond, do
     g_material[2] = gkb;
     g_material[3] = grho;
   }
+  if (g_wind)
+    for (int a = 0; a < 3; ++a) g_wind[a] = gw[a];
   if (g_x0) std::copy(ax.begin(), ax.end(), g_x0);
   if (g_v0) std::copy(av.begin(), av.end(), g_v0);
   if (status) *status = worst;

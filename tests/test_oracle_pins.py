@@ -501,3 +501,96 @@ def test_adjoint_velocity_increments_matches_finite_differences(oracle_mod):
             a[key] = a[key] + e * d
             return _rollout_loss(sim, mat, a["x0"], a["v0"], a["forces"], target, dt, T, tol, force_mode=1)[0]
         check(_richardson(f, 1e-3 * scale), float((gr[key] * d).sum()), key)
+
+
+# ----------------------------------------------------------------- air drag (wind)
+def test_drag_terminal_velocity(oracle_mod):
+    """An unpinned sheet falling through still air reaches the terminal velocity where
+    drag balances gravity: m g + rho_air A |d|_e d = 0 with d = -v and m = rho A, i.e.
+    |v|_e v = (rho / rho_air) g.  Implicit Euler's fixed point (dv = 0) is exactly that
+    balance, whatever the step."""
+    sim, rest = _small_sheet(oracle_mod, 5, "none")
+    dt, T = 1.0 / 30.0, 200
+    rho_air = 1.0
+    tx, tv, _, st = sim.forward(MAT, rest, np.zeros_like(rest), None, dt=dt, steps=T, tol=1e-13, max_iter=2000,
+                                gravity=W.GRAVITY, air_density=rho_air, wind=np.zeros(3))
+    assert st == 0
+    a = MAT[3] / rho_air * 9.8
+    eps = 1e-3
+    # s sqrt(s^2 + eps^2) = a  =>  s^2 = (-eps^2 + sqrt(eps^4 + 4 a^2)) / 2
+    s = np.sqrt((-eps ** 2 + np.sqrt(eps ** 4 + 4 * a * a)) / 2)
+    np.testing.assert_allclose(tv[-1], np.broadcast_to([0.0, 0.0, -s], rest.shape), atol=1e-10)
+
+
+def test_drag_galilean_invariance(oracle_mod):
+    """Wind w on a sheet starting at v0 = 0 is the same motion as still air with the sheet
+    starting at -w, seen from a frame moving with the wind: x^w_t = x^0_t + t h w and
+    v^w_t = v^0_t + w (internal forces see only relative positions, H annihilates uniform
+    velocities, drag sees only v - w)."""
+    rng = np.random.default_rng(9)
+    sim, rest = _small_sheet(oracle_mod, 5, "none")
+    x0 = rest + 0.01 * rng.normal(size=rest.shape)
+    dt, T = 1.0 / 30.0, 12
+    w = np.array([0.7, -0.3, 0.2])
+    kw = dict(dt=dt, steps=T, tol=1e-13, max_iter=5000, gravity=W.GRAVITY, air_density=1.0)
+    txw, tvw, _, _ = sim.forward(MAT, x0, np.zeros_like(rest), None, wind=w, **kw)
+    tx0, tv0, _, _ = sim.forward(MAT, x0, np.broadcast_to(-w, rest.shape), None, wind=np.zeros(3), **kw)
+    for t in range(T + 1):
+        np.testing.assert_allclose(txw[t], tx0[t] + t * dt * w, atol=1e-10)
+        np.testing.assert_allclose(tvw[t], tv0[t] + w, atol=1e-10)
+
+
+def test_drag_zero_density_is_no_drag(oracle_mod):
+    rng = np.random.default_rng(2)
+    sim, rest = _small_sheet(oracle_mod, 4, "top2")
+    kw = dict(dt=1 / 30, steps=5, tol=1e-13, max_iter=5000, gravity=W.GRAVITY)
+    a = sim.forward(MAT, rest, np.zeros_like(rest), None, **kw)
+    b = sim.forward(MAT, rest, np.zeros_like(rest), None, air_density=0.0, wind=rng.normal(size=3), **kw)
+    np.testing.assert_array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("force_mode", [0, 1])
+def test_adjoint_with_drag_matches_finite_differences(oracle_mod, force_mode):
+    """Air drag on (rho_air = 1, wind 0.5 m/s sideways plus a seeded part): the adjoint's
+    gradients w.r.t. the wind components, Y, kb, rho, the forces (or increments), x0 and
+    v0 against Richardson-extrapolated central differences of the forward map."""
+    rng = np.random.default_rng(40 + force_mode)
+    N, T = 4, 6
+    rest, tris = W.grid_mesh(N)
+    pin = W.pins(N, "top2")
+    sim = oracle_mod.OracleSim(rest, tris, pin)
+    dt, tol = 1.0 / 30.0, 1e-13
+    mat = MAT.copy()
+    F = (1e-4 if force_mode == 0 else 1e-3) * rng.normal(size=(T, sim.n, 3))
+    w = np.array([0.5, 0.0, 0.1]) + 0.1 * rng.normal(size=3)
+    x0, v0 = rest.copy(), np.zeros_like(rest)
+    kw = dict(dt=dt, steps=T, tol=tol, max_iter=20000, gravity=W.GRAVITY, force_mode=force_mode, air_density=1.0)
+    target = sim.forward(mat * np.array([2.0, 1.0, 0.5, 1.0]), x0, v0, F, wind=w * 0.5, **kw)[0]
+
+    def loss(m=mat, x=x0, v=v0, f=F, wi=w):
+        tx = sim.forward(m, x, v, f, wind=wi, **kw)[0]
+        return oracle_mod.loss_l2(tx, target)[0]
+
+    tx, tv, _, _ = sim.forward(mat, x0, v0, F, wind=w, **kw)
+    L, dL = oracle_mod.loss_l2(tx, target)
+    gr = sim.backward(mat, tx, tv, dL, forces=F, wind=w, **kw)
+    assert gr["status"] == 0
+
+    def check(fd, an, what):
+        assert an == pytest.approx(fd, rel=2e-6, abs=1e-9 * max(1.0, abs(L))), what
+
+    for k in range(3):
+        e = np.zeros(3); e[k] = 1.0
+        check(_richardson(lambda h: loss(wi=w + h * e), 1e-3), gr["wind"][k], f"wind{k}")
+    for k, name in ((0, "Y"), (2, "kb"), (3, "rho")):
+        def f(h, k=k):
+            m2 = mat.copy(); m2[k] += h
+            return loss(m=m2)
+        check(_richardson(f, 1e-3 * mat[k]), gr["material"][k], name)
+    free = (pin == 0)[:, None].astype(float)
+    dF = rng.normal(size=F.shape) * free
+    dx = rng.normal(size=rest.shape)
+    dv = rng.normal(size=rest.shape) * free
+    check(_richardson(lambda h: loss(f=F + h * dF), 1e-3 * np.abs(F).max()), float((gr["forces"] * dF).sum()), "forces")
+    check(_richardson(lambda h: loss(x=x0 + h * dx), 1e-6), float((gr["x0"] * dx).sum()), "x0")
+    check(_richardson(lambda h: loss(v=v0 + h * dv), 1e-6), float((gr["v0"] * dv).sum()), "v0")
