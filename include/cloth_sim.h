@@ -106,6 +106,12 @@ typedef struct cloth_opts {
                                the form the paper's implementation details give its
                                corrective forces, Sec. 3.4); the backward then returns dL/dF_t
                                in the same sense                                      */
+  double air_density;       /* rho_air [kg/m^3] >= 0; > 0 adds the air drag of the
+                               relative wind velocity d = w - v on every free vertex,
+                               f = rho_air A s(d) d with its lumped rest area A and
+                               s(d) = (|d|^2 + (1e-3 m/s)^2)^1/2, implicit through
+                               df/dv in the step matrix (Eq. 5); the paper fixes it at
+                               1 kg/m^3 and optimises the wind (Sec. 3.4).  0 = none  */
 } cloth_opts;
 
 #define CLOTH_FORCES_FORCE 0
@@ -216,6 +222,17 @@ int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* 
  * counts the nonzero blocks (9 values + column each) and its vector traffic for the
  * schedule in use.  No device work; error INVALID_ARG for another id. */
 int cloth_kernel_bytes(cloth_batch* batch, int32_t kernel, int64_t* bytes);
+
+/* Wind velocity per sheet for the air drag (cloth_opts.air_density > 0): device
+ * [count][3] in the batch precision [m/s], or NULL for still air.  The pointer is kept
+ * and read by every later cloth_forward and cloth_backward (recompute and adjoint), so
+ * its contents must stay unchanged until the matching cloth_backward has been issued;
+ * no device work. */
+int cloth_set_wind(cloth_batch* batch, const void* wind);
+
+/* dL/dw of the last cloth_backward: device [count][3] in the batch precision, written
+ * on `stream` (zero without air drag). */
+int cloth_wind_gradient(cloth_batch* batch, void* g_wind, void* stream);
 
 /* ---- single-kernel entry points (parity checks of each stage) ---- */
 

@@ -56,6 +56,7 @@ void cloth_default_opts(cloth_opts* o) {
   o->cg_schedule = -1;
   o->cg_handover = 0;
   o->force_mode = CLOTH_FORCES_FORCE;
+  o->air_density = 0.0;
 }
 
 int cloth_mesh_create(const double* rest_xyz, int32_t n, const int32_t* tris, int32_t m, const uint8_t* pinned,
@@ -95,7 +96,8 @@ int cloth_batch_create(const cloth_mesh* const* meshes, int32_t count, const clo
       !(o.clamp_eta >= 0.0) || (o.exec != CLOTH_EXEC_PLAIN && o.exec != CLOTH_EXEC_GRAPH) || o.cg_poll_every < 1 ||
       (o.precond != CLOTH_PRECOND_JACOBI && o.precond != CLOTH_PRECOND_BLOCK_JACOBI) || o.cg_schedule < -1 ||
       o.cg_schedule > 7 || o.cg_handover < 0 ||
-      (o.force_mode != CLOTH_FORCES_FORCE && o.force_mode != CLOTH_FORCES_VELOCITY))
+      (o.force_mode != CLOTH_FORCES_FORCE && o.force_mode != CLOTH_FORCES_VELOCITY) ||
+      !(o.air_density >= 0.0))
     return fail(CLOTH_ERR_INVALID_ARG, "cloth_batch_create: invalid option value");
   std::vector<const cloth::MeshData*> sheets;
   for (int i = 0; i < count; ++i) {
@@ -174,6 +176,16 @@ int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks, 
                       int32_t* cg_schedule) {
   CLOTH_NEED_BATCH("cloth_matrix_info");
   return batch->engine->matrix_info(rows, blocks, stored_blocks, cg_schedule);
+}
+
+int cloth_set_wind(cloth_batch* batch, const void* wind) {
+  CLOTH_NEED_BATCH("cloth_set_wind");
+  return batch->engine->set_wind(wind);
+}
+
+int cloth_wind_gradient(cloth_batch* batch, void* g_wind, void* stream) {
+  CLOTH_NEED_BATCH("cloth_wind_gradient");
+  return batch->engine->wind_gradient(g_wind, stream);
 }
 
 int cloth_kernel_bytes(cloth_batch* batch, int32_t kernel, int64_t* bytes) {

@@ -87,6 +87,10 @@ struct Dev {
   unsigned long long* body_runs;  // [3] CG loop-body executions per phase
   unsigned* sheet_iters;          // [3][S][2] per phase and sheet: largest solve, sum over solves
   double* gacc;  // [S][3] dL/dY, dL/dkb, dL/drho
+  double* gacc_w;  // [S][3] dL/dw (wind velocity)
+  double* row_w;   // [Np][3] per-vertex shares of dL/dw (adjoint scratch)
+  double air_density;  // > 0: air drag of the relative wind on every free vertex
+  const R* wind;       // [S][3] wind velocity per sheet, or null (still air)
   // parameters
   R h, gx, gy, gz, eta;
   double tol;
@@ -625,8 +629,41 @@ __device__ __forceinline__ void gather_block(const Dev<R>& d, int ent, R (&Hb)[9
 // The element kernels stored f_e - h H~_e v_e per element vertex, so
 // b_i = h (sum_e (f_e - h H~_e v_e)_i + m_i g + F_i)  (= h (f + M g + F) - h^2 H~ v).
 // Fext: user-layout external force of this step or null.
+// Air drag on a free vertex: the air moves at the sheet's wind velocity w; the vertex
+// with lumped rest area A feels f = rho_air A s(d) d for the relative air velocity
+// d = w - v, with the smoothed speed s(d) = sqrt(|d|^2 + eps^2).  df/dv = -rho_air A G(d),
+// G(d) = s I + d d^T / s, symmetric positive definite: it adds h rho_air A G to the
+// vertex's diagonal block of the step matrix (Eq. 5 with df/dv nonzero).
+constexpr double kAirEps = 1e-3;  // m/s
+
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __restrict__ Fext) {
+__device__ __forceinline__ V3<double> relative_wind(const Dev<R>& d, int s, V3<double> v) {
+  const V3<double> w = d.wind ? V3<double>{(double)d.wind[3 * s], (double)d.wind[3 * s + 1], (double)d.wind[3 * s + 2]}
+                              : V3<double>{0.0, 0.0, 0.0};
+  return {w.x - v.x, w.y - v.y, w.z - v.z};
+}
+
+__device__ __forceinline__ double air_speed(V3<double> r) { return sqrt(r.x * r.x + r.y * r.y + r.z * r.z + kAirEps * kAirEps); }
+
+// G(r) a
+__device__ __forceinline__ V3<double> air_G(V3<double> r, V3<double> a) {
+  const double s = air_speed(r), ra = (r.x * a.x + r.y * a.y + r.z * a.z) / s;
+  return {s * a.x + ra * r.x, s * a.y + ra * r.y, s * a.z + ra * r.z};
+}
+
+// the vector k -> a^T (dG/dr_k) b
+__device__ __forceinline__ V3<double> air_dG(V3<double> r, V3<double> a, V3<double> b) {
+  const double s = air_speed(r);
+  const double ab = a.x * b.x + a.y * b.y + a.z * b.z, ar = a.x * r.x + a.y * r.y + a.z * r.z;
+  const double rb = r.x * b.x + r.y * b.y + r.z * b.z, k = ar * rb / (s * s * s);
+  return {r.x * ab / s + (a.x * rb + ar * b.x) / s - k * r.x, r.y * ab / s + (a.y * rb + ar * b.y) / s - k * r.y,
+          r.z * ab / s + (a.z * rb + ar * b.z) / s - k * r.z};
+}
+
+// v: the velocity the step starts from (FP64, internal layout), or null (no drag terms)
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __restrict__ Fext,
+                                                      const double* __restrict__ v) {
   const int w = blockIdx.x;
   const int s = d.work_sheet[w];
   if (threadIdx.x >= d.work_rows[w]) return;
@@ -675,12 +712,27 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
 #pragma unroll
     for (int q = 0; q < 9; ++q) dst[q * 32] = zero ? R(0) : h2 * Hb[q];
   }
+  // air drag: h rho_air A G(d) on the diagonal block, the force into b
+  double dg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  V3<double> fw = {0.0, 0.0, 0.0};
+  if (d.air_density > 0.0 && v && !pin_i) {
+    const V3<double> r = relative_wind(d, s, ld3(v, i));
+    const double c = d.air_density * (double)d.area3[i], sp = air_speed(r), hc = (double)d.h * c;
+    const double rr[3] = {r.x, r.y, r.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) dg[3 * a + q] = hc * ((a == q ? sp : 0.0) + rr[a] * rr[q] / sp);
+    fw = {c * sp * r.x, c * sp * r.y, c * sp * r.z};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dblk[q] += dg[q];
+  }
   {
     R* dst = d.Aval + (size_t)base * 32 * 9 + lane;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const R dq = (q == 0 || q == 4 || q == 8) ? (pin_i ? R(1) : mass) : R(0);
-      dst[q * 32] = pin_i ? dq : dq - h2 * rsum[q];
+      dst[q * 32] = pin_i ? dq : dq + (R)dg[q] - h2 * rsum[q];
     }
   }
   V3<R> b = {R(0), R(0), R(0)};
@@ -688,9 +740,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Dev<R> d, const R* __rest
     const int u = d.i2u[i];
     V3<R> fe = Fext && u >= 0 ? ld3(Fext, u) : V3<R>{R(0), R(0), R(0)};
     const double h = (double)d.h, md = (double)mass;
-    b.x = (R)(h * (f.x + md * (double)d.gx + (double)fe.x));
-    b.y = (R)(h * (f.y + md * (double)d.gy + (double)fe.y));
-    b.z = (R)(h * (f.z + md * (double)d.gz + (double)fe.z));
+    b.x = (R)(h * (f.x + md * (double)d.gx + (double)fe.x + fw.x));
+    b.y = (R)(h * (f.y + md * (double)d.gy + (double)fe.y + fw.y));
+    b.z = (R)(h * (f.z + md * (double)d.gz + (double)fe.z + fw.z));
   }
   st3(d.bvec, i, b);
   // preconditioner: inverse of the 3x3 diagonal block (adjugate / determinant, in FP64)
@@ -1368,8 +1420,21 @@ __global__ void k_adj_vertex(Dev<R> d, double* __restrict__ ax, double* __restri
   const double h = (double)d.h;
   st3(ax, i, V3<double>{a_x.x + (double)r1.x + (double)dl.x, a_x.y + (double)r1.y + (double)dl.y,
                         a_x.z + (double)r1.z + (double)dl.z});
-  const V3<double> nv = {a_v.x + h * a_x.x + (double)r2.x, a_v.y + h * a_x.y + (double)r2.y,
-                         a_v.z + h * a_x.z + (double)r2.z};
+  V3<double> nv = {a_v.x + h * a_x.x + (double)r2.x, a_v.y + h * a_x.y + (double)r2.y,
+                   a_v.z + h * a_x.z + (double)r2.z};
+  // air drag: b depends on w and on the starting velocity through f, A through G(d);
+  // q = h rho_air A (G lam - dG[lam, dv]) goes to the wind gradient and leaves v_bar
+  V3<double> qw = {0.0, 0.0, 0.0};
+  if (d.air_density > 0.0 && !d.pinned[i]) {
+    const V3<double> vs = ld3(v_t, i), vn1 = ld3(v_t1, i);
+    const V3<double> r = relative_wind(d, d.vsheet[i], vs);
+    const V3<double> dvi = {vn1.x - vs.x, vn1.y - vs.y, vn1.z - vs.z};
+    const V3<double> gl = air_G(r, lam), tl = air_dG(r, lam, dvi);
+    const double hc = h * d.air_density * (double)d.area3[i];
+    qw = {hc * (gl.x - tl.x), hc * (gl.y - tl.y), hc * (gl.z - tl.z)};
+    nv = {nv.x - qw.x, nv.y - qw.y, nv.z - qw.z};
+  }
+  if (d.row_w) st3(d.row_w, i, qw);
   st3(av, i, nv);
   if (gF_row && u >= 0) {
     if (fmode == 0) st3(gF_row, u, V3<R>{(R)(h * lam.x), (R)(h * lam.y), (R)(h * lam.z)});
@@ -1386,15 +1451,25 @@ __global__ void k_adj_vertex(Dev<R> d, double* __restrict__ ax, double* __restri
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_param_acc(Dev<R> d) {
   const int s = blockIdx.x;
-  double v[3] = {0.0, 0.0, 0.0};
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int t = d.sheet_toff[s] + threadIdx.x; t < d.sheet_toff[s + 1]; t += kThreads) v[0] += d.tri_sc[t];
   for (int e = d.sheet_hoff[s] + threadIdx.x; e < d.sheet_hoff[s + 1]; e += kThreads) v[1] += d.hin_sc[e];
-  for (int i = d.sheet_voff[s] + threadIdx.x; i < d.sheet_voff[s + 1]; i += kThreads) v[2] += d.row_sc[i];
-  block_sum<3>(v);
+  for (int i = d.sheet_voff[s] + threadIdx.x; i < d.sheet_voff[s + 1]; i += kThreads) {
+    v[2] += d.row_sc[i];
+    if (d.air_density > 0.0) {
+      v[3] += d.row_w[3 * (size_t)i];
+      v[4] += d.row_w[3 * (size_t)i + 1];
+      v[5] += d.row_w[3 * (size_t)i + 2];
+    }
+  }
+  block_sum<6>(v);
   if (threadIdx.x == 0) {
     d.gacc[3 * s] += v[0];
     d.gacc[3 * s + 1] += v[1];
     d.gacc[3 * s + 2] += v[2];
+    d.gacc_w[3 * s] += v[3];
+    d.gacc_w[3 * s + 1] += v[4];
+    d.gacc_w[3 * s + 2] += v[5];
   }
 }
 
@@ -1406,6 +1481,13 @@ __global__ void k_grad_material(Dev<R> d, R* __restrict__ g) {
   g[4 * s + 1] = R(0);
   g[4 * s + 2] = (R)d.gacc[3 * s + 1];
   g[4 * s + 3] = (R)d.gacc[3 * s + 2];
+}
+
+template <class R>
+__global__ void k_grad_wind(Dev<R> d, R* __restrict__ g) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.S) return;
+  for (int k = 0; k < 3; ++k) g[3 * s + k] = (R)d.gacc_w[3 * s + k];
 }
 
 // ------------------------------------------------------------------ test-only kernels

@@ -26,6 +26,8 @@ class EngineBase {
   virtual int matrix_info(int64_t* rows, int64_t* blocks, int64_t* slots, int32_t* schedule) = 0;
   virtual int time_kernel(int which, int reps, double* avg_ms, void* stream) = 0;
   virtual int kernel_bytes(int which, int64_t* bytes) = 0;
+  virtual int set_wind(const void* wind) = 0;
+  virtual int wind_gradient(void* g_wind, void* stream) = 0;
   virtual int internal_forces(const void* material, const void* x, void* fm, void* fb, void* stream) = 0;
   virtual int system_dense(const void* material, const void* x, const void* v, const void* F, void* A, void* b,
                            void* stream) = 0;

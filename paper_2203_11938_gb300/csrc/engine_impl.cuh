@@ -157,6 +157,10 @@ class Engine final : public EngineBase {
     d.body_runs = alloc<unsigned long long>(3, &rc);
     d.sheet_iters = alloc<unsigned>(6 * (size_t)L_.S, &rc);
     d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
+    d.gacc_w = alloc<double>(3 * (size_t)L_.S, &rc);
+    d.air_density = o_.air_density;
+    d.wind = nullptr;
+    if (o_.air_density > 0.0) d.row_w = alloc<double>(n3, &rc);
     // the state (x, v) is carried in FP64 in both precisions
     seg_x_ = alloc<double>(n3 * (C_ + 1), &rc);
     seg_v_ = alloc<double>(n3 * (C_ + 1), &rc);
@@ -283,9 +287,10 @@ class Engine final : public EngineBase {
     cudaStream_t st = (cudaStream_t)stream_;
     last_stream_ = st;
     d_.material = mat_;
+    d_.wind = wind_;
     fwd_forces_ = forces;
     if (o_.exec == CLOTH_EXEC_GRAPH) {
-      GraphKey key{0, {material, x0, v0, forces, traj_x, status, nullptr, nullptr, nullptr, nullptr}, 0};
+      GraphKey key{0, {material, x0, v0, forces, traj_x, status, wind_, nullptr, nullptr, nullptr}, 0};
       CLOTH_TRY(run_graph(key, st, &fixed_fwd_, [&](cudaStream_t s) {
         return forward_body(material, x0, v0, forces, traj_x, status, s, true);
       }));
@@ -313,9 +318,10 @@ class Engine final : public EngineBase {
     cudaStream_t st = (cudaStream_t)stream_;
     last_stream_ = st;
     d_.material = mat_;
+    d_.wind = wind_;
     const int seg_valid = seg_valid_;
     if (o_.exec == CLOTH_EXEC_GRAPH) {
-      GraphKey key{1, {fwd_forces_, dL_dx, g_material, g_forces, g_x0, g_v0, status, nullptr, nullptr, nullptr},
+      GraphKey key{1, {fwd_forces_, dL_dx, g_material, g_forces, g_x0, g_v0, status, wind_, nullptr, nullptr},
                    seg_valid};
       CLOTH_TRY(run_graph(key, st, &fixed_bwd_, [&](cudaStream_t s) {
         return backward_body(dL_dx, g_material, g_forces, g_x0, g_v0, status, s, true, seg_valid);
@@ -338,6 +344,19 @@ class Engine final : public EngineBase {
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
     if (launches) *launches = fixed_fwd_ + fixed_bwd_ + (sched_fused_ ? 4 : 5) * (int64_t)(b[0] + b[1] + b[2]);
+    return CLOTH_OK;
+  }
+
+  int set_wind(const void* wind) override {
+    wind_ = (const R*)wind;
+    d_.wind = wind_;
+    return CLOTH_OK;
+  }
+
+  int wind_gradient(void* g, void* stream) override {
+    if (!g) return invalid("cloth_wind_gradient: null output");
+    launch(k_grad_wind<R>, dim3((L_.S + 127) / 128), dim3(128), (cudaStream_t)stream, d_, (R*)g);
+    CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
 
@@ -420,7 +439,7 @@ class Engine final : public EngineBase {
           else k_cg_spmv<R, false><<<spmv_grid_, kThreads, 0, st>>>(d_);
           break;
         case 1: k_cg_update<R><<<upd_grid_, kThreads, 0, st>>>(d_); break;
-        case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr); break;
+        case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr, nullptr); break;
         case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
         default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
       }
@@ -613,7 +632,7 @@ class Engine final : public EngineBase {
     gather_state((const R*)v, tmp_vd_, st);
     const double* vs = start_velocity(tmp_vd_, (const R*)F, st);
     elements(tmp_xd_, vs, st);
-    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, o_.force_mode == CLOTH_FORCES_VELOCITY ? nullptr : (const R*)F);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, o_.force_mode == CLOTH_FORCES_VELOCITY ? nullptr : (const R*)F, vs);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
@@ -721,7 +740,7 @@ class Engine final : public EngineBase {
     CLOTH_CUDA(cudaMemset(tmp_vd_, 0, sizeof(double) * n3()));
     d_.material = mat_tmp_;
     elements(tmp_xd_, tmp_vd_, st);
-    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr);
+    k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr, nullptr);
     // loop schedules: the best of three rounds of 30 iterations each (bit 2 is decided below)
     float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
     const int iters = 30;
@@ -918,7 +937,7 @@ class Engine final : public EngineBase {
     const double* v = start_velocity(v0, F, st);
     if (o_.force_mode == CLOTH_FORCES_VELOCITY) F = nullptr;
     elements(x, v, st);
-    launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, F);
+    launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, F, v);
     CLOTH_CUDA(cudaGetLastError());
     CLOTH_TRY(solve(d_.bvec, phase, st, cap));
     launch(k_state_update<R>, dim3(grid_rows()), dim3(256), st, d_, x, v, xn, vn, traj_row);
@@ -965,6 +984,7 @@ class Engine final : public EngineBase {
     launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseBackward);
     launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseRecompute);
     CLOTH_CUDA(cudaMemsetAsync(d_.gacc, 0, sizeof(double) * 3 * L_.S, st));
+    CLOTH_CUDA(cudaMemsetAsync(d_.gacc_w, 0, sizeof(double) * 3 * L_.S, st));
     gather_state((const R*)dL_dx + (size_t)T_ * nu3, ax_, st);
     CLOTH_CUDA(cudaMemsetAsync(av_, 0, sizeof(double) * n3(), st));
     const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
@@ -984,15 +1004,15 @@ class Engine final : public EngineBase {
       for (int t = t1 - 1; t >= t0; --t) {
         const int j = t - t0;
         // A_t at x_t (the RHS of the step matrix is not needed)
+        const double* vstart = start_velocity(sv(j), force_row(fwd_forces_, t), st);
         elements(sx(j), nullptr, st);
-        launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, (const R*)nullptr);
+        launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, (const R*)nullptr, vstart);
         launch(k_adj_rhs<R>, dim3(grid_rows()), dim3(256), st, d_, (const double*)ax_, (const double*)av_);
         CLOTH_CUDA(cudaGetLastError());
         CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap));
         if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         if (L_.E) launch(k_adj_hinge<R>, dim3(ge), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         R* gF = g_forces ? (R*)g_forces + (size_t)t * nu3 : nullptr;
-        const double* vstart = start_velocity(sv(j), force_row(fwd_forces_, t), st);
         launch(k_adj_vertex<R>, dim3(grid_rows()), dim3(256), st, d_, ax_, av_, vstart, (const double*)sv(j + 1),
                (const R*)dL_dx + (size_t)t * nu3, gF, (int)o_.force_mode);
         launch(k_param_acc<R>, dim3(L_.S), dim3(kThreads), st, d_);
@@ -1055,6 +1075,7 @@ class Engine final : public EngineBase {
   double *seg_x_ = nullptr, *seg_v_ = nullptr, *ck_x_ = nullptr, *ck_v_ = nullptr;
   double *tmp_xd_ = nullptr, *tmp_vd_ = nullptr, *tmp_ud_ = nullptr;
   double* vin_ = nullptr;  // a step's starting velocity v_t + F_t (velocity-increment forces)
+  const R* wind_ = nullptr;  // per-sheet wind velocity [S][3] given by cloth_set_wind
   double *ax_ = nullptr, *av_ = nullptr;
   R *tmp_a_ = nullptr, *tmp_b_ = nullptr;
   R *mat_ = nullptr, *mat_tmp_ = nullptr;

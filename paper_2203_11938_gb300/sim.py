@@ -32,7 +32,7 @@ EXPORTS = (
     "cloth_batch_destroy", "cloth_batch_info", "cloth_forward", "cloth_backward", "cloth_loss_l2",
     "cloth_loss_pinhole", "cloth_stats", "cloth_internal_forces", "cloth_system_dense", "cloth_spmv",
     "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel", "cloth_loss_l2_static",
-    "cloth_sheet_iterations", "cloth_kernel_bytes",
+    "cloth_sheet_iterations", "cloth_kernel_bytes", "cloth_set_wind", "cloth_wind_gradient",
 )
 
 
@@ -52,6 +52,7 @@ class ClothOpts(ctypes.Structure):
         ("cg_schedule", ctypes.c_int32),
         ("cg_handover", ctypes.c_int32),
         ("force_mode", ctypes.c_int32),
+        ("air_density", ctypes.c_double),
     ]
 
 
@@ -87,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_matrix_info.argtypes = [_vp] * 5
     lib.cloth_sheet_iterations.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
     lib.cloth_kernel_bytes.argtypes = [_vp, ctypes.c_int32, _vp]
+    lib.cloth_set_wind.argtypes = [_vp, _vp]
+    lib.cloth_wind_gradient.argtypes = [_vp, _vp, _vp]
     lib.cloth_time_kernel.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.cloth_internal_forces.argtypes = [_vp] * 6
     lib.cloth_system_dense.argtypes = [_vp] * 8
@@ -152,7 +155,7 @@ class ClothBatch:
 
     def __init__(self, meshes, *, steps, dt, precision="f32", cg_tol=1e-6, cg_max_iter=2000, checkpoint_every=0,
                  gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16, precond="block",
-                 cg_schedule=-1, cg_handover=0, force_mode="force"):
+                 cg_schedule=-1, cg_handover=0, force_mode="force", air_density=0.0):
         import torch
 
         if not torch.cuda.is_available():
@@ -175,6 +178,7 @@ class ClothBatch:
         o.cg_schedule = int(cg_schedule)
         o.cg_handover = int(cg_handover)
         o.force_mode = {"force": 0, "velocity": 1}[force_mode]
+        o.air_density = float(air_density)
         self.opts = o
         self.steps = int(steps)
         self.dtype = torch.float64 if precision == "f64" else torch.float32
@@ -310,6 +314,20 @@ class ClothBatch:
         _check(_lib.cloth_time_kernel(self._h, self.KERNELS[name], int(reps), ctypes.byref(ms), self._stream()),
                "cloth_time_kernel")
         return ms.value
+
+    def set_wind(self, wind):
+        """Per-sheet wind velocity [count, 3] (device, batch precision) or None; kept by
+        reference and read by the following forward and backward calls."""
+        if wind is not None:
+            self._t(wind, (self.count, 3), "wind")
+        self._wind = wind
+        _check(_lib.cloth_set_wind(self._h, _ptr(wind)), "cloth_set_wind")
+
+    def wind_gradient(self):
+        """dL/dw of the last backward, [count, 3]."""
+        g = self._new(self.count, 3)
+        _check(_lib.cloth_wind_gradient(self._h, _ptr(g), self._stream()), "cloth_wind_gradient")
+        return g
 
     def kernel_bytes(self, name):
         """Algorithmic bytes of one launch of the kernel time_kernel(name) times."""

@@ -37,11 +37,11 @@ def test_header_declarations_are_exported(lib):
 
 def test_opts_struct_layout_matches_header(lib):
     o = sim.default_opts()
-    assert ctypes.sizeof(sim.ClothOpts) == 88  # = sizeof(cloth_opts) in C (checked with gcc)
+    assert ctypes.sizeof(sim.ClothOpts) == 96  # = sizeof(cloth_opts) in C (checked with gcc)
     assert o.precision == sim.FP32 and o.steps == 1 and o.cg_max_iter == 2000
     assert o.gravity[2] == pytest.approx(-9.8) and o.clamp_eta == pytest.approx(1e-3)
     assert o.exec == sim.EXEC_GRAPH and o.cg_poll_every == 16 and o.precond == 1 and o.cg_schedule == -1
-    assert o.cg_handover == 0 and o.force_mode == 0
+    assert o.cg_handover == 0 and o.force_mode == 0 and o.air_density == 0.0
 
 
 def test_mesh_create_counts(lib):
@@ -82,7 +82,7 @@ def test_batch_create_rejects_bad_options_on_host(lib):
     for field, value in (("steps", 0), ("dt", -1.0), ("cg_max_iter", 0), ("precision", 7), ("exec", 9),
                          ("clamp_eta", -1.0), ("cg_poll_every", 0), ("precond", 5),
                          ("cg_schedule", 8), ("cg_schedule", -2), ("cg_handover", -1),
-                         ("force_mode", 2)):
+                         ("force_mode", 2), ("air_density", -1.0)):
         o = sim.default_opts()
         setattr(o, field, value)
         rc = lib.cloth_batch_create(arr, 1, ctypes.byref(o), ctypes.byref(h))

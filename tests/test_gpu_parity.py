@@ -224,6 +224,59 @@ def test_velocity_increment_forces_match_oracle(oracle_mod, prec):
     assert np.all(gF[:, pin] == 0.0)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_air_drag_matches_oracle(oracle_mod, prec):
+    """Air drag of a wind (rho_air = 1 kg/m^3, wind 0.5 m/s sideways and 0.1 m/s up) on the
+    10x10 sheet with seeded forces, 20 steps, against the oracle with the same drag:
+    FP64 positions to 1e-10 m and gradients (material, forces, x0, v0, wind) to 1e-9;
+    FP32 positions to 1e-5 m and gradients to 1e-3.  Checkpoint-and-recompute (every 3
+    steps) gives bitwise the same gradients."""
+    from paper_2203_11938_gb300 import sim
+
+    cfg = W.config1()
+    s = cfg.sheets[0]
+    T = cfg.steps
+    rng = np.random.Generator(np.random.PCG64(11))
+    F = 1e-4 * rng.normal(size=(T, s.n, 3))
+    w = np.array([0.5, 0.0, 0.1])
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    rnd = (lambda a: np.asarray(a, np.float32).astype(np.float64)) if prec == "f32" else (lambda a: np.asarray(a))
+    x0, Fi, mat, wi = rnd(s.rest), rnd(F), rnd(s.material), rnd(w)
+    tol = 1e-12 if prec == "f64" else 1e-8
+    o = oracle_sims(oracle_mod, cfg.sheets)[0]
+    kw = dict(dt=cfg.dt, steps=T, tol=1e-12, max_iter=20000, gravity=W.GRAVITY, air_density=1.0)
+    tx, tv, _, st = o.forward(mat, x0, np.zeros_like(x0), Fi, wind=wi, **kw)
+    target = o.forward(mat * np.array(cfg.target_scale), x0, np.zeros_like(x0), Fi, wind=0.5 * wi, **kw)[0]
+    _, dL = oracle_mod.loss_l2(tx, target)
+    go = o.backward(mat, tx, tv, dL, forces=Fi, wind=wi, **kw)
+    assert st == 0 and go["status"] == 0
+    res = []
+    for ckpt in (0, 3):
+        b = sim.ClothBatch([(s.rest, s.tris, s.pinned)], steps=T, dt=cfg.dt, precision=prec, cg_tol=tol,
+                           cg_max_iter=20000, checkpoint_every=ckpt, air_density=1.0)
+        b.set_wind(to_cuda(wi[None], dtype))
+        traj, status = b.forward(to_cuda(mat[None], dtype), to_cuda(x0, dtype),
+                                 torch.zeros(s.n, 3, dtype=dtype, device="cuda"), to_cuda(Fi, dtype))
+        _, dLg = b.loss_l2(traj, to_cuda(target, dtype))
+        g = b.backward(dLg)
+        gw = b.wind_gradient()
+        torch.cuda.synchronize()
+        assert int(status[0]) == 0 and int(g["status"][0]) == 0
+        res.append((to_np(traj), to_np(g["material"])[0], to_np(g["forces"]), to_np(g["x0"]), to_np(g["v0"]),
+                    to_np(gw)[0]))
+    for a, c in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, c)
+    traj, gm, gF, gx, gv, gwv = res[0]
+    pos_tol, g_tol = (1e-10, 1e-9) if prec == "f64" else (1e-5, 1e-3)
+    assert np.abs(traj - tx).max() <= pos_tol
+    for k in (0, 2, 3):
+        assert gm[k] == pytest.approx(go["material"][k], rel=g_tol), k
+    assert rel(gF, go["forces"]) < g_tol
+    assert rel(gx, go["x0"]) < g_tol
+    assert rel(gv, go["v0"]) < g_tol
+    assert rel(gwv, go["wind"]) < g_tol
+
+
 def test_config2_fp32_positions_and_gradients(oracle_mod):
     """32x32 sheet, top edge pinned, 60 steps of 1/60 s with seeded per-vertex forces,
     FP32 path (CG tol 1e-8) vs the FP64 oracle (tol 1e-10) run on the same inputs (the
