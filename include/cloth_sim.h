@@ -260,6 +260,30 @@ int cloth_spmv(cloth_batch* batch, const void* material, const void* x, const vo
 int cloth_third_contraction(cloth_batch* batch, const void* material, const void* x,
                             const void* a, const void* b, void* out, void* stream);
 
+/* ---- image energies of a sheet (Sec. 3.2) ----
+ *
+ * Soft rasterisation of one textured sheet and its photometric and silhouette energies,
+ * E = E_p + lambda E_s, E_p = sum_pixels |I - I_hat|_1 (RGB), E_s = sum_pixels
+ * |G(A) - G(B_hat)|_1 with G the Gaussian filter of 7 px (lambda = 0.5), and dE/dx.
+ * The rasteriser: coverage sigmoid(+-d^2 / 1 px^2) of each projected triangle (d: distance
+ * of the pixel centre to its nearest edge, + inside), silhouette A = 1 - prod(1 - D),
+ * bilinear texture colour at the clamped barycentric uv, blended against a black
+ * background with weights D exp(zn / 1e-4) (zn: normalised inverse depth, 1 at 0.5 m,
+ * 0 at 5 m; background zn 1e-3).  Camera: the pinhole of cloth_loss_pinhole with the
+ * principal point at the image centre, pixel centres at (u + 1/2, v + 1/2).
+ * n vertices, m triangles: tris HOST [m][3] (validated: INVALID_ARG if out of range);
+ * x device [n][3], uv device [n][2] (texture coordinates in [0, 1]^2, v down the
+ * texture), tex device [tex_h][tex_w][3], camera HOST double[4] (f, cx, cy, cz);
+ * image device [H][W][3], mask device [H][W] (the input frame and its foreground mask);
+ * scratch: device, cloth_image_energy_scratch(n, m, W, H) bytes, 8-byte aligned;
+ * energy: device double[1]; dE_dx: device [n][3] or NULL; out_image [H][W][3] and
+ * out_silhouette [H][W]: device or NULL.  All arrays double; all work on `stream`. */
+size_t cloth_image_energy_scratch(int32_t n, int32_t m, int32_t W, int32_t H);
+int cloth_image_energy(int32_t n, int32_t m, const int32_t* tris, const double* x, const double* uv,
+                       int32_t tex_w, int32_t tex_h, const double* tex, const double* camera, int32_t W,
+                       int32_t H, const double* image, const double* mask, void* scratch, double* energy,
+                       double* dE_dx, double* out_image, double* out_silhouette, void* stream);
+
 /* ---- allocation-free variant (the paper has no counterpart) ----
  *
  * cloth_loss_l2_static computes exactly what cloth_loss_l2 computes (same kernels,

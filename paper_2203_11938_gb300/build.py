@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libcloth_sim.so")
-SOURCES = ["prep.cpp", "api.cpp", "engine_f32.cu", "engine_f64.cu", "noalloc.cu"]
+SOURCES = ["prep.cpp", "api.cpp", "engine_f32.cu", "engine_f64.cu", "noalloc.cu", "render.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -33,6 +33,7 @@ EXPORTS = (
     "cloth_loss_pinhole", "cloth_stats", "cloth_internal_forces", "cloth_system_dense", "cloth_spmv",
     "cloth_third_contraction", "cloth_last_error", "cloth_matrix_info", "cloth_time_kernel", "cloth_loss_l2_static",
     "cloth_sheet_iterations", "cloth_kernel_bytes", "cloth_set_wind", "cloth_wind_gradient",
+    "cloth_image_energy_scratch", "cloth_image_energy",
 )
 
 
@@ -89,6 +90,11 @@ def load_library(path: str = LIB_PATH):
     lib.cloth_sheet_iterations.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
     lib.cloth_kernel_bytes.argtypes = [_vp, ctypes.c_int32, _vp]
     lib.cloth_set_wind.argtypes = [_vp, _vp]
+    lib.cloth_image_energy_scratch.argtypes = [ctypes.c_int32] * 4
+    lib.cloth_image_energy_scratch.restype = ctypes.c_size_t
+    lib.cloth_image_energy.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                       _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                       _vp]
     lib.cloth_wind_gradient.argtypes = [_vp, _vp, _vp]
     lib.cloth_time_kernel.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
     lib.cloth_internal_forces.argtypes = [_vp] * 6
@@ -411,6 +417,35 @@ def _autograd_function():
 
 
 _CT = None
+
+
+def image_energy(x, tris, uv, tex, camera, image, mask, want_grad=True, want_render=False):
+    """Image energy E = E_p + 0.5 E_s of one sheet against one frame (cloth_image_energy):
+    x [n, 3], uv [n, 2], tex [Ht, Wt, 3], image [H, W, 3], mask [H, W] (CUDA float64
+    tensors), tris [m, 3] int (host), camera (f, cx, cy, cz).  Returns (E [1], dE/dx [n, 3]
+    or None, rendered image or None, silhouette or None)."""
+    import numpy as np
+    import torch
+
+    load_library()
+    for t, name in ((x, "x"), (uv, "uv"), (tex, "tex"), (image, "image"), (mask, "mask")):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError(f"{name}: expected a contiguous CUDA float64 tensor")
+    tr = np.ascontiguousarray(np.asarray(tris, np.int32))
+    n, m = x.shape[0], tr.shape[0]
+    H, W = mask.shape
+    scratch = torch.empty(int(_lib.cloth_image_energy_scratch(n, m, W, H)) // 8 + 1, dtype=torch.float64,
+                          device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(n, 3, dtype=torch.float64, device="cuda") if want_grad else None
+    img = torch.empty(H, W, 3, dtype=torch.float64, device="cuda") if want_render else None
+    sil = torch.empty(H, W, dtype=torch.float64, device="cuda") if want_render else None
+    cam = (ctypes.c_double * 4)(*[float(c) for c in camera])
+    stream = torch.cuda.current_stream().cuda_stream
+    _check(_lib.cloth_image_energy(n, m, tr.ctypes.data_as(_vp), _ptr(x), _ptr(uv), tex.shape[1], tex.shape[0],
+                                   _ptr(tex), cam, W, H, _ptr(image), _ptr(mask), _ptr(scratch), _ptr(E), _ptr(g),
+                                   _ptr(img), _ptr(sil), _vp(stream)), "cloth_image_energy")
+    return E, g, img, sil
 
 
 def cloth_trajectory(batch, material, x0, v0, forces=None):
