@@ -12,7 +12,8 @@ tensors).  Readings of the paper:
   per-window iteration cap is reached; afterwards the next frame is added as soon as the
   latest active frame's energy drops below b, or when the cap is reached.
 * The energy of frame t is the pinhole reprojection energy sum_i |pi(x_t^i) - u_t^i|^2
-  (the stand-in for the image energies, Eq. 7-8).  The simulation runs the full
+  of tracked points, or (image_frame_loss) the paper's image energy E_p + 0.5 E_s of the
+  soft-rasterised sheet against the input frame and its mask.  The simulation runs the full
   trajectory every iteration; frames after the active one get zero loss gradient, which
   gives the same gradient as simulating only the active frames.
 * Adam with learning rate 1e-3 on log Y, log k_b, log rho (the parameters span decades)
@@ -75,6 +76,35 @@ def frame_energies(traj, tracks, camera):
     return (d * d).sum(dim=(1, 2))
 
 
+def image_frame_loss(images, masks, tris, uv, tex, camera, energy_fn=None):
+    """Per-frame loss of a one-sheet batch against input frames: the image energy
+    E_p + 0.5 E_s of each frame t >= 1 (cloth_image_energy).  images[t] [H, W, 3] and
+    masks[t] [H, W] (CUDA float64), tris [m, 3] (host), uv [n, 2], tex [Ht, Wt, 3].
+    energy_fn(x_t, t) -> (E, dE/dx_t) replaces the library call (tests).  Returns
+    loss(traj) -> (per-frame energies [T+1], dL/dx [T+1, n, 3])."""
+
+    def gpu_energy(xt, t):
+        from . import sim
+
+        E, g, _, _ = sim.image_energy(xt, tris, uv, tex, camera, images[t], masks[t])
+        return E[0], g
+
+    fn = energy_fn or gpu_energy
+
+    def loss(traj):
+        import torch
+
+        e = torch.zeros(traj.shape[0], dtype=torch.float64)
+        dL = torch.zeros_like(traj)
+        for t in range(1, traj.shape[0]):
+            E, g = fn(traj[t].double().contiguous(), t)
+            e[t] = float(E)
+            dL[t] = g.to(traj.dtype)
+        return e, dL
+
+    return loss
+
+
 @dataclass
 class FitResult:
     material: np.ndarray       # [S, 4]
@@ -84,10 +114,12 @@ class FitResult:
 
 
 def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr=1e-3, first=5, max_iters=50,
-        optimise_forces=True):
+        optimise_forces=True, frame_loss=None):
     """Adam over (log Y, log k_b, log rho) of every sheet and the per-step forces, with
     the adaptive window.  batch: a sim.ClothBatch; material0 [S, 4], x0/v0 [N, 3],
-    tracks [T+1, N, 2] (device tensors of the batch's precision)."""
+    tracks [T+1, N, 2] (device tensors of the batch's precision) for the pinhole-track
+    loss, or frame_loss(traj) -> (per-frame energies [T+1], dL/dx [T+1, N, 3]) in its
+    place (e.g. image_frame_loss; tracks and camera are then unused)."""
     import torch
 
     dtype = x0.dtype
@@ -108,10 +140,13 @@ def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr
         mat.copy_(torch.stack([m[:, 0], nu.double(), m[:, 1], m[:, 2]], dim=1))
         Fc.copy_(F.detach())
         traj, status = batch.forward(mat, x0, v0, Fc)
-        _, dL = batch.loss_pinhole(traj, tracks, camera)
+        if frame_loss is None:
+            _, dL = batch.loss_pinhole(traj, tracks, camera)
+            e = frame_energies(traj, tracks, camera)
+        else:
+            e, dL = frame_loss(traj)
         dL[window.active + 1:] = 0  # frames after the active one do not take part
         g = batch.backward(dL)
-        e = frame_energies(traj, tracks, camera)
         history.append((window.active, float(e[1:window.active + 1].sum())))
         opt.zero_grad()
         gm = g["material"].double()
@@ -119,7 +154,7 @@ def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr
         if optimise_forces:
             F.grad = g["forces"].double()
         opt.step()
-        window.step(e.cpu().numpy())
+        window.step(np.asarray(e.detach().cpu() if hasattr(e, "cpu") else e, dtype=np.float64))
     m = torch.exp(logm.detach())
     mat = torch.stack([m[:, 0], nu.double(), m[:, 1], m[:, 2]], dim=1)
     return FitResult(mat.cpu().numpy(), F.detach().cpu().numpy(), history, window)

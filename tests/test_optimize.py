@@ -131,3 +131,81 @@ def test_fit_masks_inactive_frames_and_steps_log_parameters():
     moved = np.log(r.material[0, [0, 2, 3]]) - np.log(start[0, [0, 2, 3]].numpy())
     np.testing.assert_allclose(moved, -lr * np.sign(g.numpy()), rtol=1e-6)
     assert r.material[0, 1] == pytest.approx(0.3)
+
+
+def test_fit_with_image_frame_loss_masks_and_assembles_frames():
+    """fit() with image_frame_loss on the stand-in batch (the oracle's image energy
+    injected in place of the library call): the adjoint receives each active frame's
+    dE/dx_t and zeros after the active window."""
+    torch = pytest.importorskip("torch")
+    from oracle import softras as S
+    from paper_2203_11938_gb300.optimize import fit, image_frame_loss
+
+    T, n = 7, 4
+    b = _FakeBatch(torch, T, n)
+    x0 = torch.tensor([[0.2, 0.2, 0.0], [0.8, 0.2, 0.0], [0.8, 0.8, 0.0], [0.2, 0.8, 0.0]], dtype=torch.float64)
+    tris = [(0, 1, 2), (0, 2, 3)]
+    uv = np.array([[0.0, 1.0], [1.0, 1.0], [1.0, 0.0], [0.0, 0.0]])
+    tex = np.random.default_rng(6).uniform(0, 1, (4, 4, 3))
+    cam = (20.0, 0.5, 0.5, 2.0)
+    truth = torch.tensor([[1.0e3, 0.3, 1e-4, 0.1]], dtype=torch.float64)
+    traj_t, _ = b.forward(truth, x0, None, None)
+    frames = [S.render(traj_t[t].numpy(), tris, uv, tex, cam, 16, 16) for t in range(T + 1)]
+    images = [f[0] for f in frames]
+    masks = [(f[1] > 0.5).double() for f in frames]
+
+    def energy_fn(xt, t):
+        E, g = S.energy_and_grad(torch.stack([xt, xt]), tris, uv, tex, cam, [None, images[t]], [None, masks[t]])
+        return E, torch.as_tensor(g[1])
+
+    loss = image_frame_loss(images, masks, tris, uv, tex, cam, energy_fn=energy_fn)
+    start = truth * torch.tensor([1.3, 1.0, 1.0, 1.0], dtype=torch.float64)
+    fit(b, start, x0, torch.zeros_like(x0), None, None, iters=1, lr=1e-3, first=5, max_iters=10,
+        optimise_forces=False, frame_loss=loss)
+    dL = b.seen[0]
+    traj0, _ = b.forward(start, x0, None, None)
+    for t in range(1, T + 1):
+        if t <= 5:
+            _, g = energy_fn(traj0[t], t)
+            np.testing.assert_allclose(dL[t].numpy(), g.numpy(), rtol=1e-12, atol=0)
+        else:
+            assert torch.all(dL[t] == 0)
+    assert torch.any(dL[1:6] != 0)
+
+
+@pytest.mark.gpu
+def test_fit_from_image_frames():
+    """4x4 sheet, 8 steps, FP64: frames rendered (by the oracle) from a ground-truth
+    trajectory; Adam with the image energy E_p + 0.5 E_s of every active frame, through
+    cloth_image_energy and the adjoint, lowers the energy of all frames."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import softras as S
+    from paper_2203_11938_gb300 import sim, workloads as W
+    from paper_2203_11938_gb300.optimize import fit, image_frame_loss
+
+    N, T, dt = 4, 8, 1.0 / 30.0
+    rest, tris = W.grid_mesh(N)
+    tri = [tuple(int(i) for i in t) for t in tris]
+    b = sim.ClothBatch([(rest, tris, W.pins(N, "top2"))], steps=T, dt=dt, precision="f64", cg_tol=1e-10,
+                       cg_max_iter=5000)
+    cam = (30.0, 0.5, 0.5, 2.0)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    uv = np.c_[rest[:, 0], 1.0 - rest[:, 1]]
+    tex = np.random.default_rng(12).uniform(0, 1, (8, 8, 3))
+    truth = cu([[2.0e3, 0.3, 2e-4, 0.1]])
+    x0 = cu(rest)
+    v0 = torch.zeros_like(x0)
+    traj_t = b.forward(truth, x0, v0)[0].cpu().numpy()
+    frames = [S.render(traj_t[t], tri, uv, tex, cam, 20, 20) for t in range(T + 1)]
+    images = [cu(f[0].numpy()) for f in frames]
+    masks = [cu((f[1].numpy() > 0.5).astype(np.float64)) for f in frames]
+    loss = image_frame_loss(images, masks, tris, cu(uv), cu(tex), cam)
+    start = truth * cu([1.5, 1.0, 0.6, 1.0])
+    e0 = float(loss(b.forward(start, x0, v0)[0])[0][1:].sum())
+    r = fit(b, start, x0, v0, None, None, iters=25, lr=3e-2, first=5, max_iters=4, optimise_forces=False,
+            frame_loss=loss)
+    e1 = float(loss(b.forward(torch.as_tensor(r.material, device="cuda").contiguous(), x0, v0)[0])[0][1:].sum())
+    assert r.window.active > 5
+    assert e1 < e0
