@@ -90,3 +90,23 @@ def test_batch_create_rejects_bad_options_on_host(lib):
     assert lib.cloth_batch_create(arr, 0, ctypes.byref(sim.default_opts()), ctypes.byref(h)) == -1
     assert lib.cloth_forward(None, None, None, None, None, None, None, None) == -1
     assert lib.cloth_backward(None, None, None, None, None, None, None, None) == -1
+
+
+def test_host_validation_of_the_newer_entry_points(lib):
+    """Entry points added for the force modes, the wind and the image energies reject a
+    null batch or bad arguments on the host, before any device work."""
+    p = ctypes.c_void_p(1)  # never dereferenced: validation fails first
+    assert lib.cloth_set_wind(None, None) == -1
+    assert lib.cloth_wind_gradient(None, p, None) == -1
+    assert lib.cloth_sheet_iterations(None, 0, None, None) == -1
+    assert lib.cloth_kernel_bytes(None, 0, None) == -1
+    cam = (ctypes.c_double * 4)(30.0, 0.5, 0.5, 2.0)
+    bad = np.array([[0, 1, 5]], np.int32)  # vertex 5 of a 3-vertex mesh
+    good = np.array([[0, 1, 2]], np.int32)
+    args = lambda n, tris: (n, tris.shape[0], tris.ctypes.data_as(ctypes.c_void_p), p, p, 4, 4, p, cam, 8, 8, p, p,  # noqa: E731
+                            p, p, None, None, None, None)
+    assert lib.cloth_image_energy(*args(3, bad)) == -1
+    assert "out of range" in lib.cloth_last_error().decode()
+    assert lib.cloth_image_energy(*args(2, good)) == -1
+    # scratch: 12 W H + 15 n doubles and the 3 m triangle indices
+    assert lib.cloth_image_energy_scratch(3, 1, 8, 8) == 8 * (12 * 64 + 15 * 3 + 2)
