@@ -200,3 +200,20 @@ def config5(steps=200, N=256):
 def grid_counts(N):
     """(vertices, triangles, interior edges) of an N x N grid."""
     return N * N, 2 * (N - 1) ** 2, 2 * N * (N - 1) + (N - 1) ** 2 - 4 * (N - 1)
+
+
+def template_tracks(rest, steps, scale=250.0, centre=(0.5, 0.5)):
+    """Synthetic 2-D tracks [steps + 1, n, 2] in pixels: every frame holds the template's
+    (x, y) coordinates mapped affinely to the image plane, u = scale (x - cx),
+    v = -scale (y - cy).  With the default camera (f = 500 px, 2 m above the sheet's
+    centre) these are where the flat template would be seen, so the tracks ask the
+    sheet to stay flat; they need no simulation and no stored data."""
+    rest = np.asarray(rest, np.float64)
+    uv = np.stack([scale * (rest[:, 0] - centre[0]), -scale * (rest[:, 1] - centre[1])], axis=1)
+    return np.broadcast_to(uv, (steps + 1,) + uv.shape).copy()
+
+
+# Sheets of the 256-sheet batch (config4, seed 1) with stored full-trajectory oracle
+# values: the largest grid (64 x 64) and the one the FP64 oracle needs the most CG
+# iterations for (61 x 61, the largest Y (N - 1)^2 / rho of the batch).
+BATCH_GOLDEN_SHEETS = {"largest": 93, "slowest": 220}

@@ -144,6 +144,40 @@ def test_lumped_mass_totals(oracle_mod):
     assert (m > 0).all()
 
 
+def _grid_vertex_mass(a, b, N, rho):
+    """Lumped mass of grid vertex (a, b) of the alternating-diagonal N x N sheet (Eq. 3:
+    each triangle gives a third of rho A0 to each of its corners), counted from the
+    geometry alone.  Cell (i, j) is cut along the diagonal from (i, j) to (i+1, j+1) when
+    i + j is even, else from (i+1, j) to (i, j+1); a corner on the cut belongs to both of
+    the cell's triangles, the other two corners to one each.  A0 = h^2 / 2, h = 1/(N-1)."""
+    h = 1.0 / (N - 1)
+    count = 0
+    for i, j in ((a - 1, b - 1), (a, b - 1), (a - 1, b), (a, b)):
+        if not (0 <= i < N - 1 and 0 <= j < N - 1):
+            continue
+        ends = {(i, j), (i + 1, j + 1)} if (i + j) % 2 == 0 else {(i + 1, j), (i, j + 1)}
+        count += 2 if (a, b) in ends else 1
+    return rho * count * (h * h / 2.0) / 3.0
+
+
+@pytest.mark.parametrize("N", [2, 3, 6, 7, 12])
+def test_lumped_mass_per_vertex_closed_form(oracle_mod, N):
+    """Every vertex's lumped mass against the count of incident triangles on the grid:
+    interior vertices alternate between 8 triangles (i + j even: every surrounding cell is
+    cut through them) and 4 (odd), edge and corner vertices take the cells that exist.
+    A mass lumped onto the wrong corners keeps the total and fails here."""
+    rest, tris = W.grid_mesh(N)
+    sim = oracle_mod.OracleSim(rest, tris)
+    rho = 0.37
+    m = sim.mass(rho)
+    expect = np.array([_grid_vertex_mass(k % N, k // N, N, rho) for k in range(N * N)])
+    np.testing.assert_allclose(m, expect, rtol=1e-13, atol=0)
+    if N >= 4:  # the two interior classes really differ (8 vs 4 triangles)
+        h2 = (1.0 / (N - 1)) ** 2
+        assert m[1 * N + 1] == pytest.approx(rho * 8 * h2 / 6, rel=1e-13)
+        assert m[1 * N + 2] == pytest.approx(rho * 4 * h2 / 6, rel=1e-13)
+
+
 def test_forces_zero_at_rest_net_force_torque(oracle_mod):
     rng = np.random.default_rng(5)
     sim, rest = _small_sheet(oracle_mod, 6, "none")
