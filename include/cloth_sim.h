@@ -15,7 +15,8 @@
  * energies open; this library uses an isotropic St. Venant-Kirchhoff membrane
  * on the Green strain (stretch stiffness Y [N/m], Poisson ratio nu) and a
  * dihedral-angle bending energy 1/2 k_b w_e (theta - theta_rest)^2 per interior
- * edge with w_e = 3 |e|^2 / (A_1 + A_2).  df/dv = 0 (no damping or drag).
+ * edge with w_e = 3 |e|^2 / (A_1 + A_2).  df/dv = 0 unless the optional air drag
+ * (cloth_opts.air_density > 0) is on; its velocity Jacobian then enters Eq. 5.
  *
  * Conventions for every entry point:
  *   - Return value: CLOTH_OK (0) or a negative CLOTH_ERR_* code; on error a
@@ -33,7 +34,8 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous with respect to the host unless stated otherwise.
  *   - Pinned vertices keep dv = 0 (kinematic pins): their velocity never
- *     changes, so with v0 = 0 they stay at x0.
+ *     changes, so with v0 = 0 they stay at x0; a nonzero v0 on a pinned vertex sets
+ *     CLOTH_STATUS_PINNED_VELOCITY_NONZERO in its sheet's status word.
  */
 #ifndef CLOTH_SIM_H
 #define CLOTH_SIM_H
@@ -58,6 +60,11 @@ extern "C" {
 #define CLOTH_STATUS_CG_MAXITER 1     /* a solve stopped at cg_max_iter            */
 #define CLOTH_STATUS_INDEFINITE 2     /* p^T A p <= 0 met inside CG                */
 #define CLOTH_STATUS_NONFINITE 4      /* NaN/Inf in a CG scalar                    */
+#define CLOTH_STATUS_PINNED_VELOCITY_NONZERO 8 /* cloth_forward: v0 is nonzero (or not
+                                         finite) on a pinned vertex of the sheet.  Pins
+                                         are kinematic (dv = 0), so such a vertex moves
+                                         at its v0 for the whole trajectory instead of
+                                         staying at x0; the run itself continues      */
 
 /* ---- options ---- */
 #define CLOTH_FP32 0
@@ -297,8 +304,10 @@ int cloth_image_energy(int32_t n, int32_t m, const int32_t* tris, const double* 
  * (512 KiB) that every GPU loading this library holds until the process exits; calls
  * with count * steps > 65,536 (or count or steps > 65,535) fail with
  * CLOTH_ERR_INVALID_ARG.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array: calls whose kernels overlap on the
+ * address (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not call this entry
+ * point on a device after a cudaDeviceReset of it (the kept address is then stale).
+ * Devices with an index of 64 or more are rejected with CLOTH_ERR_INVALID_ARG.  All calls share the one array: calls whose kernels overlap on the
  * GPU (e.g. issued to different streams without ordering) race and give wrong losses.
  * count: sheets; sheet_offsets: device [count + 1] int32, vertex offset of each sheet in
  * the packed user layout (sheet_offsets[count] = n_total); steps, n_total: as in

@@ -1263,6 +1263,17 @@ __global__ void k_state_update(Dev<R> d, const double* __restrict__ x, const dou
   if (traj_row && u >= 0) st3(traj_row, u, V3<R>{(R)x1.x, (R)x1.y, (R)x1.z});
 }
 
+// A pinned vertex keeps its starting velocity (dv = 0): flag a sheet whose pinned vertices
+// do not start at rest (their pins would drift), including non-finite values.
+template <class R>
+__global__ void k_check_pins(Dev<R> d, const double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np || !d.pinned[i]) return;
+  const V3<double> w = ld3(v, i);
+  if (!(w.x == 0.0 && w.y == 0.0 && w.z == 0.0))
+    atomicOr(&d.cg[d.vsheet[i]].status, (int)CLOTH_STATUS_PINNED_VELOCITY_NONZERO);
+}
+
 template <class R>
 __global__ void k_reset_status(Dev<R> d, int phase) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;

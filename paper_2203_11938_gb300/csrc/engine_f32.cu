@@ -1,5 +1,6 @@
-// FP32 instantiation of the cloth engine (element kernels, SpMV and CG vectors in
-// float; CG dot products, residual norms and gradient reductions in double).
+// FP32 instantiation of the cloth engine (element Hessians, the assembled matrix, SpMV and
+// CG vectors in float; CG dot products, residual norms, alpha and the CG solution in
+// float-float; state, element force vectors and gradient reductions in double).
 #include "engine_impl.cuh"
 
 namespace cloth {

@@ -956,6 +956,7 @@ class Engine final : public EngineBase {
     launch(k_reset_status<R>, dim3((L_.S + 255) / 256), dim3(256), st, d_, (int)kPhaseForward);
     gather_state((const R*)x0, sx(0), st);
     gather_state((const R*)v0, sv(0), st);
+    launch(k_check_pins<R>, dim3(grid_rows()), dim3(256), st, d_, (const double*)sv(0));
     CLOTH_CUDA(cudaMemcpyAsync(traj_x, x0, sizeof(R) * nu3, cudaMemcpyDeviceToDevice, st));
     for (int k = 0; k < nseg_; ++k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);

@@ -24,13 +24,21 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of the static array for the current device (first call per device does
-// the lookup).  Returns CLOTH_OK or CLOTH_ERR_CUDA.
+// the lookup and keeps it for the life of the process; a cudaDeviceReset of that device
+// unloads the module, after which the kept address is stale, so the entry point must not
+// be used on a device after it was reset).  Returns CLOTH_OK, CLOTH_ERR_INVALID_ARG or
+// CLOTH_ERR_CUDA.
 int static_partials(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     set_last_error(std::string("cloth_loss_l2_static: cudaGetDevice failed: ") + cudaGetErrorString(e));
     return CLOTH_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_last_error("cloth_loss_l2_static: device index " + std::to_string(dev) + " is beyond the " +
+                   std::to_string(kMaxDevices) + " devices this entry point keeps an address for");
+    return CLOTH_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {

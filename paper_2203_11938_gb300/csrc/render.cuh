@@ -52,8 +52,10 @@ struct Camera {
 };
 
 // image point and inverse depth of a vertex; J: d(px, py, inv)/d(x, y, z), row-major 3x3
+// A vertex at or behind the camera (depth <= 0) gets NaN image point, inverse depth and
+// Jacobian, so the frame's energy and gradient come out NaN (as the tracking loss does).
 RS_HD void project(const Camera& c, const double* x, P2* q, double* inv, double* J) {
-  const double dep = c.cz - x[2], id = 1.0 / dep;
+  const double dep = c.cz - x[2], id = dep > 0.0 ? 1.0 / dep : NAN;
   q->x = 0.5 * c.W + c.f * (x[0] - c.cx) * id;
   q->y = 0.5 * c.H - c.f * (x[1] - c.cy) * id;
   *inv = id;
@@ -97,9 +99,11 @@ RS_HD void seg_d2_grad(P2 p, P2 a, P2 b, double g, P2* ga, P2* gb) {
 // bilinear texture sample (tex [Ht][Wt][3]) at (u, v); dC/du, dC/dv when wanted
 RS_HD void sample(const double* tex, int Wt, int Ht, double u, double v, double* C, double* dCdu, double* dCdv) {
   double x = u * Wt - 0.5, y = v * Ht - 0.5;
-  const bool cx = x < 0.0 || x > Wt - 1.0, cy = y < 0.0 || y > Ht - 1.0;  // clamped: no gradient
-  x = x < 0.0 ? 0.0 : (x > Wt - 1.0 ? Wt - 1.0 : x);
-  y = y < 0.0 ? 0.0 : (y > Ht - 1.0 ? Ht - 1.0 : y);
+  const bool cx = !(x >= 0.0 && x <= Wt - 1.0), cy = !(y >= 0.0 && y <= Ht - 1.0);  // clamped: no gradient
+  // written so that a NaN coordinate (degenerate projected triangle) clamps to texel 0
+  // and never reaches the integer conversion
+  x = !(x >= 0.0) ? 0.0 : (x > Wt - 1.0 ? Wt - 1.0 : x);
+  y = !(y >= 0.0) ? 0.0 : (y > Ht - 1.0 ? Ht - 1.0 : y);
   int x0 = (int)floor(x), y0 = (int)floor(y);
   const int xm = Wt > 1 ? Wt - 2 : 0, ym = Ht > 1 ? Ht - 2 : 0;
   x0 = x0 > xm ? xm : x0;
@@ -301,6 +305,9 @@ RS_HD void pixel_backward(const Scene& s, P2 p, const double* gI, double gA, Add
     corners(s, j, q, inv, uv);
     TriPix t;
     tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
+    // a triangle whose coverage underflowed to 0 contributes exactly nothing here (its
+    // weight, the coverage derivative D (1 - D) and its colour share are all 0)
+    if (t.D == 0.0) continue;
     const double e = exp((t.zn - top) / GAMMA), w = t.D * e;
     const double gw = (gI[0] * (t.C[0] - I[0]) + gI[1] * (t.C[1] - I[1]) + gI[2] * (t.C[2] - I[2])) / S;
     const double gC[3] = {gI[0] * w / S, gI[1] * w / S, gI[2] * w / S};

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcloth_sim.so")
 
 FP32, FP64 = 0, 1
 EXEC_PLAIN, EXEC_GRAPH = 0, 1
-STATUS_CG_MAXITER, STATUS_INDEFINITE, STATUS_NONFINITE = 1, 2, 4
+STATUS_CG_MAXITER, STATUS_INDEFINITE, STATUS_NONFINITE, STATUS_PINNED_VELOCITY_NONZERO = 1, 2, 4, 8
 
 # exported names declared in include/cloth_sim.h
 EXPORTS = (
@@ -427,12 +427,30 @@ def image_energy(x, tris, uv, tex, camera, image, mask, want_grad=True, want_ren
     import numpy as np
     import torch
 
-    load_library()
+    # shapes first (the kernels index x as [n][3], uv as [n][2], tex as [Ht][Wt][3],
+    # image as [H][W][3] with n, H, W taken from x and mask), then devices and types
+    tr = np.ascontiguousarray(np.asarray(tris, np.int32))
+    if tr.ndim != 2 or tr.shape[1] != 3:
+        raise ClothError(f"tris must have shape [m, 3], got {tuple(tr.shape)}")
+    for t, name in ((x, "x"), (uv, "uv"), (tex, "tex"), (image, "image"), (mask, "mask")):
+        if not isinstance(t, torch.Tensor):
+            raise ClothError(f"{name} must be a torch tensor")
+    if x.ndim != 2 or x.shape[1] != 3:
+        raise ClothError(f"x must have shape [n, 3], got {tuple(x.shape)}")
+    n = x.shape[0]
+    if tuple(uv.shape) != (n, 2):
+        raise ClothError(f"uv must have shape {(n, 2)}, got {tuple(uv.shape)}")
+    if tex.ndim != 3 or tex.shape[2] != 3:
+        raise ClothError(f"tex must have shape [Ht, Wt, 3], got {tuple(tex.shape)}")
+    if mask.ndim != 2:
+        raise ClothError(f"mask must have shape [H, W], got {tuple(mask.shape)}")
+    if tuple(image.shape) != tuple(mask.shape) + (3,):
+        raise ClothError(f"image must have shape {tuple(mask.shape) + (3,)}, got {tuple(image.shape)}")
     for t, name in ((x, "x"), (uv, "uv"), (tex, "tex"), (image, "image"), (mask, "mask")):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-            raise ValueError(f"{name}: expected a contiguous CUDA float64 tensor")
-    tr = np.ascontiguousarray(np.asarray(tris, np.int32))
-    n, m = x.shape[0], tr.shape[0]
+            raise ClothError(f"{name}: expected a contiguous CUDA float64 tensor")
+    load_library()
+    m = tr.shape[0]
     H, W = mask.shape
     scratch = torch.empty(int(_lib.cloth_image_energy_scratch(n, m, W, H)) // 8 + 1, dtype=torch.float64,
                           device="cuda")

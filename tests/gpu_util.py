@@ -52,3 +52,12 @@ def sheets_mixed(seed=3):
         rest, tris = W.grid_mesh(N)
         out.append(W.Sheet(N, rest, tris, W.pins(N, pin), W.sample_material(rng), None))
     return out
+
+
+def max_entry_err(a, b):
+    """Largest entry-wise difference, relative to the largest entry of the reference: a
+    localised error in a few entries shows here even where the norm of the whole field
+    hides it."""
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)

@@ -110,3 +110,25 @@ def test_host_validation_of_the_newer_entry_points(lib):
     assert lib.cloth_image_energy(*args(2, good)) == -1
     # scratch: 12 W H + 15 n doubles and the 3 m triangle indices
     assert lib.cloth_image_energy_scratch(3, 1, 8, 8) == 8 * (12 * 64 + 15 * 3 + 2)
+
+
+def test_image_energy_binding_rejects_wrong_shapes_before_any_launch():
+    """sim.image_energy checks every array's shape against x, mask and the texture before
+    it checks devices or calls the library, so a grey frame, a 4-channel texture or too
+    few uv rows never reach a kernel (which would index past their ends)."""
+    torch = pytest.importorskip("torch")
+    n, H, W = 9, 6, 5
+    f = lambda *s: torch.zeros(*s, dtype=torch.float64)  # noqa: E731
+    good = dict(x=f(n, 3), tris=np.array([[0, 1, 2]], np.int32), uv=f(n, 2), tex=f(4, 4, 3), camera=(500, 0, 0, 2),
+                image=f(H, W, 3), mask=f(H, W))
+    bad = {
+        "x": dict(x=f(n, 2)), "uv": dict(uv=f(n - 1, 2)), "tex": dict(tex=f(4, 4, 4)),
+        "image": dict(image=f(H, W)), "mask": dict(mask=f(H, W, 1)), "tris": dict(tris=np.array([0, 1, 2], np.int32)),
+    }
+    for name, change in bad.items():
+        args = dict(good, **change)
+        with pytest.raises(sim.ClothError, match="shape"):
+            sim.image_energy(**args)
+    # right shapes on the CPU: rejected for the device, still before any launch
+    with pytest.raises(sim.ClothError, match="CUDA"):
+        sim.image_energy(**good)

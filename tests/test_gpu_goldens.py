@@ -1,0 +1,138 @@
+"""Full-size FP32 parity against stored FP64 oracle values (tests/golden/*.npz, written by
+tests/golden/make_fullsize_goldens.py, which calls only the oracle).
+
+Each case runs in the launch configuration bench.py times (FP32, captured graph, the
+workload's CG tolerance and autotuned schedule; checkpoint-and-recompute for the long
+sheets) on the same float-rounded inputs the oracle was given, and compares entry by
+entry: positions within 1e-5 m of the 1 m sheet after the trajectory, velocities within
+1e-4 m/s, parameter gradients (Y, k_b, rho) within 1e-3 relative, and the per-vertex
+gradients (x0, v0, forces) within 1e-3 of their norm and, entry by entry, within 1e-3 of
+the field's largest entry.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2203_11938_gb300 import workloads as W
+
+from gpu_util import make_batch, max_entry_err, rel, split, to_cuda, to_np
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+f32r = lambda a: np.asarray(a, np.float32).astype(np.float64)  # noqa: E731
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11938_gb300 import build
+
+    build.build()
+
+
+def _golden(case):
+    path = os.path.join(GOLDEN, f"{case}.npz")
+    if not os.path.exists(path):
+        pytest.fail(f"missing stored oracle values {path} (tests/golden/make_fullsize_goldens.py)")
+    g = np.load(path)
+    assert int(g["status"].max()) == 0, "the oracle run behind this golden did not converge"
+    return g
+
+
+def _check_sheet(g, x_mid, x_final, v_final, gm, gx0, gv0, gF=None, what=""):
+    sel = g["vertex_sample"]
+    err_mid = np.abs(x_mid[sel] - g["x_mid"]).max()
+    err_x = np.abs(x_final[sel] - g["x_final"]).max()
+    err_v = np.abs(v_final[sel] - g["v_final"]).max()
+    assert err_mid <= 1e-5, (what, "x_mid", err_mid)
+    assert err_x <= 1e-5, (what, "x_final", err_x)
+    assert err_v <= 1e-4, (what, "v_final", err_v)
+    for q in (0, 2, 3):
+        assert gm[q] == pytest.approx(g["g_material"][q], rel=1e-3), (what, "material", q, gm[q], g["g_material"][q])
+    for name, a in (("g_x0", gx0), ("g_v0", gv0)):
+        ref = g[name]
+        assert np.linalg.norm(a[sel] - ref) <= 1e-3 * np.linalg.norm(ref), (what, name, rel(a[sel], ref))
+        assert max_entry_err(a[sel], ref) <= 1e-3, (what, name, max_entry_err(a[sel], ref))
+    if gF is not None:
+        ref = g["g_forces"]
+        got = gF[g["g_forces_rows"]][:, sel]
+        assert rel(got, ref) <= 1e-3, (what, "g_forces", rel(got, ref))
+        assert max_entry_err(got, ref) <= 1e-3, (what, "g_forces", max_entry_err(got, ref))
+        assert np.linalg.norm(gF) == pytest.approx(float(g["g_forces_norm"]), rel=1e-3)
+    return {"x_final": err_x, "material": max(abs(gm[q] / g["g_material"][q] - 1) for q in (0, 2, 3))}
+
+
+def test_batch256_largest_and_slowest_sheets_match_stored_oracle():
+    """The whole 256-sheet batch (100 steps, FP32, CG tol 1e-7) with the loss
+    L = sum_{t>=1} |x_t - X|^2; its largest sheet (64 x 64) and the sheet the oracle needs
+    the most CG iterations for (61 x 61) against the oracle's 100-step run at tol 1e-10."""
+    cfg = W.config4()
+    gold = {k: _golden(f"batch_{k}") for k in W.BATCH_GOLDEN_SHEETS}
+    f32 = torch.float32
+    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, max_iter=cfg.cg_max_iter)
+    mat = np.stack([f32r(s.material) for s in cfg.sheets])
+    x0 = to_cuda(np.concatenate([s.rest for s in cfg.sheets]), f32)
+    traj, status = b.forward(to_cuda(mat, f32), x0, torch.zeros_like(x0), None)
+    _, dL = b.loss_l2(traj, x0.expand(traj.shape).contiguous())
+    g = b.backward(dL)
+    torch.cuda.synchronize()
+    assert int(status.max()) == 0 and int(g["status"].max()) == 0
+    T = cfg.steps
+    xs = split(to_np(traj), b.sheet_sizes, axis=1)
+    gx0 = split(to_np(g["x0"]), b.sheet_sizes)
+    gv0 = split(to_np(g["v0"]), b.sheet_sizes)
+    gm = to_np(g["material"])
+    for name, k in W.BATCH_GOLDEN_SHEETS.items():
+        gd = gold[name]
+        assert int(gd["sheet_index"]) == k and int(gd["steps"]) == T
+        v_final = (xs[k][T] - xs[k][T - 1]) / cfg.dt
+        _check_sheet(gd, xs[k][T // 2], xs[k][T], v_final, gm[k], gx0[k], gv0[k], what=name)
+    # the "slowest" sheet is among the batch's slowest on the GPU too
+    _, tot = b.sheet_iterations("forward")
+    k_slow = W.BATCH_GOLDEN_SHEETS["slowest"]
+    assert (tot > tot[k_slow]).sum() < 8, (int(tot[k_slow]), np.sort(tot)[-8:])
+
+
+def _single_sheet_case(case, cfg, steps, ckpt, loss):
+    g = _golden(case)
+    s = cfg.sheets[0]
+    f32 = torch.float32
+    assert int(g["steps"]) == steps
+    b = make_batch(cfg.sheets, steps=steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, max_iter=cfg.cg_max_iter,
+                   ckpt=ckpt)
+    x0 = to_cuda(f32r(s.rest), f32)
+    F = to_cuda(f32r(s.forces[:steps]), f32)
+    traj, st = b.forward(to_cuda(f32r(s.material), f32)[None], x0, torch.zeros_like(x0), F)
+    if loss == "pinhole":
+        uv = to_cuda(W.template_tracks(s.rest, steps), f32)
+        _, dL = b.loss_pinhole(traj, uv, cfg.camera)
+    else:
+        _, dL = b.loss_l2(traj, x0.expand(traj.shape).contiguous())
+    gr = b.backward(dL)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0 and int(gr["status"][0]) == 0
+    tr = to_np(traj)
+    v_final = (tr[steps] - tr[steps - 1]) / cfg.dt
+    return _check_sheet(g, tr[steps // 2], tr[steps], v_final, to_np(gr["material"])[0], to_np(gr["x0"]),
+                        to_np(gr["v0"]), to_np(gr["forces"]), what=case)
+
+
+def test_grid100_first_segment_matches_stored_oracle():
+    """The 100 x 100 pinhole workload's first checkpoint segment (30 steps of 1/30 s, smooth
+    wind, FP32, CG tol 1e-6, recompute every 10 steps) with the pinhole loss against the
+    template's tracks, against the oracle's 30-step run."""
+    cfg = W.config3()
+    _single_sheet_case("grid100_segment", cfg, 30, 10, "pinhole")
+
+
+def test_grid256_first_segment_matches_stored_oracle():
+    """The 256 x 256 four-corner workload's first checkpoint segment (1/60 s steps, smooth
+    wind, FP32, CG tol 1e-6, recompute every 5 steps) with L = sum |x_t - X|^2, against the
+    oracle's run (every 5th vertex stored)."""
+    cfg = W.config5()
+    steps = int(_golden("grid256_segment")["steps"])
+    _single_sheet_case("grid256_segment", cfg, steps, 5, "l2")

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_static_scratch_loss_matches_loss_l2_on_two_calls():
+def test_static_scratch_loss_matches_loss_l2_on_two_calls(oracle_mod):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2203_11938_gb300 import build, sim
@@ -51,6 +51,15 @@ def test_static_scratch_loss_matches_loss_l2_on_two_calls():
             torch.cuda.synchronize()
             np.testing.assert_allclose(loss.cpu().numpy(), ref_loss.cpu().numpy(), rtol=1e-12, atol=0)
             np.testing.assert_allclose(grad.cpu().numpy(), ref_grad.cpu().numpy(), rtol=1e-12, atol=0)
+            # and both against the oracle's loss of each sheet on the same values
+            tr, tg = traj.double().cpu().numpy(), target.double().cpu().numpy()
+            off = np.cumsum([0] + b.sheet_sizes)
+            for k in range(b.count):
+                L_o, g_o = oracle_mod.loss_l2(tr[:, off[k]:off[k + 1]], tg[:, off[k]:off[k + 1]])
+                assert float(loss[k]) == pytest.approx(L_o, rel=1e-12 if precision == "f64" else 1e-6)
+                np.testing.assert_allclose(grad.double().cpu().numpy()[:, off[k]:off[k + 1]], g_o,
+                                           rtol=1e-12 if precision == "f64" else 1e-6,
+                                           atol=1e-300 if precision == "f64" else 1e-7)
     # sizes beyond the static scratch are rejected with a clear error
     rc = lib.cloth_loss_l2_static(70000, ctypes.c_void_p(offsets.data_ptr()), 1, N, sim.FP32,
                                   ctypes.c_void_p(traj.data_ptr()), ctypes.c_void_p(traj.data_ptr()),
