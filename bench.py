@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-plain-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cold-start", action="store_true",
+                   help="every CG solve from zero instead of the previous step's solution")
     p.add_argument("--time-steps", type=int, default=0,
                    help="override the workload's time-step count (profiling runs; not a bench value)")
     return p.parse_args()
@@ -88,6 +90,11 @@ def workload_config(wl, name):
                         f"{wl.precision}, CG tol {wl.cg_tol:g} (block-Jacobi PCG, max {wl.cg_max_iter} iterations), fwd+loss+adjoint",
             "sheets": len(sizes), "vertices": wl.total_vertices, "time_steps": wl.steps,
             "checkpoint_every": wl.checkpoint_every, "loss": wl.loss}
+
+
+def solver_config(args):
+    warm = W.BENCH_CG_WARM_START and not args.cold_start
+    return {"cg_start": "previous step's solution (warm start)" if warm else "zero"}
 
 
 def units_per_step(wl):
@@ -214,7 +221,8 @@ def run_ours(args):
     dtype = torch.float32 if wl.precision == "f32" else torch.float64
     meshes = [(s.rest, s.tris, s.pinned) for s in wl.sheets]
     b = sim.ClothBatch(meshes, steps=wl.steps, dt=wl.dt, precision=wl.precision, cg_tol=wl.cg_tol,
-                       cg_max_iter=wl.cg_max_iter, checkpoint_every=wl.checkpoint_every, exec_mode=args.exec_mode)
+                       cg_max_iter=wl.cg_max_iter, checkpoint_every=wl.checkpoint_every, exec_mode=args.exec_mode,
+                       cg_warm_start=W.BENCH_CG_WARM_START and not args.cold_start)
     dev = "cuda"
     mat = torch.tensor(np.stack([s.material for s in wl.sheets]), dtype=dtype, device=dev)
     x0 = torch.tensor(np.concatenate([s.rest for s in wl.sheets]), dtype=dtype, device=dev)
@@ -368,7 +376,8 @@ def run_ours(args):
         tot_units, tot_ms = 0, 0.0
         for s in sub:
             bs = sim.ClothBatch([(s.rest, s.tris, s.pinned)], steps=wl.steps, dt=wl.dt, precision=wl.precision,
-                                cg_tol=wl.cg_tol, cg_max_iter=wl.cg_max_iter, exec_mode="plain")
+                                cg_tol=wl.cg_tol, cg_max_iter=wl.cg_max_iter, exec_mode="plain",
+                                cg_warm_start=W.BENCH_CG_WARM_START and not args.cold_start)
             m1 = torch.tensor(s.material[None], dtype=dtype, device=dev)
             xs = torch.tensor(s.rest, dtype=dtype, device=dev)
             vs = torch.zeros_like(xs)
@@ -399,7 +408,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == torch.float32 else "f64",
             "data": "synthetic (seeded grids shaped like the paper's sequences)",
-            "config": dict(workload_config(wl, args.workload),
+            "config": dict(workload_config(wl, args.workload), **solver_config(args),
                            **{"l2": f"working set {b.workspace_bytes / 1e9:.2f} GB > 129 MB L2 (inputs larger than L2)",
                               "exec": args.exec_mode}),
             "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps), "roofline": roofline, "kernels": kernels,

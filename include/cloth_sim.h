@@ -119,6 +119,13 @@ typedef struct cloth_opts {
                                s(d) = (|d|^2 + (1e-3 m/s)^2)^1/2, implicit through
                                df/dv in the step matrix (Eq. 5); the paper fixes it at
                                1 kg/m^3 and optimises the wind (Sec. 3.4).  0 = none  */
+  int32_t cg_warm_start;    /* 0: every CG solve starts from 0 (the plain method); 1: each
+                               forward solve starts from the previous step's dv and each
+                               adjoint solve from the lambda of the step after it (the first
+                               solve of a call from 0); the stopping test stays
+                               |r| <= cg_tol |b|, so results differ from the zero start by
+                               at most what the tolerance allows.  Checkpoint-and-recompute
+                               replays the same starting vectors (bitwise the same results) */
 } cloth_opts;
 
 #define CLOTH_FORCES_FORCE 0
@@ -129,7 +136,8 @@ typedef struct cloth_opts {
 
 /* Fill `opts` with defaults: FP32, 1 step, dt 1/30, tol 1e-6, 2000 iterations,
  * no checkpointing, gravity (0, 0, -9.8), clamp_eta 1e-3, GRAPH execution, poll 16,
- * block-Jacobi preconditioner, autotuned CG schedule. */
+ * block-Jacobi preconditioner, autotuned CG schedule, forces as forces, no air drag,
+ * CG from a zero start. */
 void cloth_default_opts(cloth_opts* opts);
 
 typedef struct cloth_mesh cloth_mesh;

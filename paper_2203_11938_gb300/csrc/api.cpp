@@ -57,6 +57,7 @@ void cloth_default_opts(cloth_opts* o) {
   o->cg_handover = 0;
   o->force_mode = CLOTH_FORCES_FORCE;
   o->air_density = 0.0;
+  o->cg_warm_start = 0;
 }
 
 int cloth_mesh_create(const double* rest_xyz, int32_t n, const int32_t* tris, int32_t m, const uint8_t* pinned,
@@ -97,7 +98,7 @@ int cloth_batch_create(const cloth_mesh* const* meshes, int32_t count, const clo
       (o.precond != CLOTH_PRECOND_JACOBI && o.precond != CLOTH_PRECOND_BLOCK_JACOBI) || o.cg_schedule < -1 ||
       o.cg_schedule > 7 || o.cg_handover < 0 ||
       (o.force_mode != CLOTH_FORCES_FORCE && o.force_mode != CLOTH_FORCES_VELOCITY) ||
-      !(o.air_density >= 0.0))
+      !(o.air_density >= 0.0) || (o.cg_warm_start != 0 && o.cg_warm_start != 1))
     return fail(CLOTH_ERR_INVALID_ARG, "cloth_batch_create: invalid option value");
   std::vector<const cloth::MeshData*> sheets;
   for (int i = 0; i < count; ++i) {

@@ -41,7 +41,8 @@ struct CGSheet {
   double stop_rr;         // (tol |b|)^2: the solve ends when r.r <= stop_rr
   FF rz_f, stop_f, alpha_f;
   float beta_f;
-  int iters, done, status, pad;
+  int iters, done, status;
+  int zero_rhs;  // b = 0: the solution is 0 (matters when the solve starts from a guess)
 };
 
 // CG dot-product accumulator of one thread: FP64 in FP64 mode; in FP32 mode a
@@ -76,6 +77,7 @@ struct Dev {
   double *tri_sc, *hin_sc, *row_sc;
   R *Aval, *bvec, *r, *z, *Ap;
   R* p;  // two direction buffers [2][Np][3] (p_k and p_{k-1})
+  R* pg;  // a solve's starting guess in the direction layout (warm start), or null
   R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
   double* dv;  // CG solution (dv, or lambda in the adjoint): FP64 after each solve
   float *dvh, *dvl;  // FP32 mode: the solution accumulated as float-float hi + lo [Np][3]
@@ -191,39 +193,41 @@ template <> __device__ __forceinline__ float beta_of<float>(const CGSheet& c) { 
 // Shared by the device loop's per-sheet scalar kernels and the per-sheet solver, so both
 // form alpha, beta and the stopping decisions bitwise alike.  Each returns true when the
 // sheet's solve is over (converged, or stopped with a status bit).
-// After the initial sums r.z, r.r (b = r at the start).
-template <class R> __device__ __forceinline__ bool cg_init_step(CGSheet& c, acc_t<R> rz, acc_t<R> rr, double tol);
-template <> __device__ __forceinline__ bool cg_init_step<double>(CGSheet& c, double rz, double rr, double tol) {
+// After the initial sums r.z, r.r and |b|^2 (b = r when the solve starts from 0).
+template <class R> __device__ __forceinline__ bool cg_init_step(CGSheet& c, acc_t<R> rz, acc_t<R> rr, acc_t<R> bb, double tol);
+template <> __device__ __forceinline__ bool cg_init_step<double>(CGSheet& c, double rz, double rr, double bb, double tol) {
   c.rz = rz;
   c.rr = rr;
-  c.bb = rr;
-  c.stop_rr = tol * tol * rr;
+  c.bb = bb;
+  c.stop_rr = tol * tol * bb;
   c.beta = 0.0;
   c.iters = 0;
   c.done = 0;
-  if (!isfinite(rr)) {
+  c.zero_rhs = bb == 0.0;
+  if (!isfinite(rr) || !isfinite(bb)) {
     c.status |= CLOTH_STATUS_NONFINITE;
     return true;
   }
-  return rr == 0.0 || rr <= c.stop_rr;
+  return bb == 0.0 || rr <= c.stop_rr;
 }
-template <> __device__ __forceinline__ bool cg_init_step<float>(CGSheet& c, FF rz, FF rr, double tol) {
-  const double rrd = ff_to_double(rr);
+template <> __device__ __forceinline__ bool cg_init_step<float>(CGSheet& c, FF rz, FF rr, FF bb, double tol) {
+  const double bbd = ff_to_double(bb);
   c.rz = ff_to_double(rz);
-  c.rr = rrd;
-  c.bb = rrd;
-  c.stop_rr = tol * tol * rrd;
+  c.rr = ff_to_double(rr);
+  c.bb = bbd;
+  c.stop_rr = tol * tol * bbd;
   c.rz_f = rz;
   c.stop_f = ff_from_double(c.stop_rr);
   c.beta = 0.0;
   c.beta_f = 0.f;
   c.iters = 0;
   c.done = 0;
-  if (!acc_finite(rr)) {
+  c.zero_rhs = bb.hi == 0.f;
+  if (!acc_finite(rr) || !acc_finite(bb)) {
     c.status |= CLOTH_STATUS_NONFINITE;
     return true;
   }
-  return rr.hi == 0.f || ff_le(rr, c.stop_f);
+  return bb.hi == 0.f || ff_le(rr, c.stop_f);
 }
 // After the sum p.Ap: alpha = r.z / p.Ap.
 template <class R> __device__ __forceinline__ bool cg_alpha_step(CGSheet& c, acc_t<R> pAp);
@@ -837,14 +841,17 @@ __device__ __forceinline__ acc_t<R> sheet_sum(const Dev<R>& d, const acc_t<R>* p
   return acc_bcast0(acc_warp_total(acc));
 }
 
-// Per sheet after k_cg_init: r.z, r.r, |b|^2; a sheet with b = 0 (or non-finite) is done at once.
+// Per sheet after k_cg_init (guess: after k_cg_init_guess, whose |b|^2 partials are in
+// part_c): r.z, r.r, |b|^2; a sheet with b = 0 (or non-finite), or whose guess already
+// meets the tolerance, is done at once.
 template <class R>
-__global__ void k_cg_scalar_init(Dev<R> d, int phase) {
+__global__ void k_cg_scalar_init(Dev<R> d, int phase, int guess) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (s >= d.S) return;
   const acc_t<R> rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
+  const acc_t<R> bb = guess ? sheet_sum(d, d.part_c, s) : rr;
   if ((threadIdx.x & 31) != 0) return;
-  if (cg_init_step<R>(d.cg[s], rz, rr, d.tol)) finish_sheet(d, s, phase, 0, 0);
+  if (cg_init_step<R>(d.cg[s], rz, rr, bb, d.tol)) finish_sheet(d, s, phase, 0, 0);
 }
 
 // One row of the SpMV: Ap_i = (A p_k)_i in difference form; returns p_i . Ap_i (or 0).
@@ -924,13 +931,72 @@ __device__ __forceinline__ void update_row(const Dev<R>& d, int i, acc_t<R> al, 
   rr = acc_dot3(r, r);
 }
 
-// FP32 mode: the solution as FP64, dv = hi + lo, once per solve.
+// Starting guess of a solve (FP64, internal layout): kept as the solution accumulator and,
+// rounded to the batch precision, in the gatherable layout the SpMV reads (d.pg).
 template <class R>
-__global__ void k_cg_solution(Dev<R> d) {
+__global__ void k_cg_guess(Dev<R> d, const double* __restrict__ guess) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.Np) return;
-  const V3<float> h = ld3(d.dvh, i), l = ld3(d.dvl, i);
-  st3(d.dv, i, V3<double>{(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z});
+  const V3<double> g = ld3(guess, i);
+  stp(d.pg, i, V3<R>{(R)g.x, (R)g.y, (R)g.z});
+  if constexpr (std::is_same<R, float>::value) {
+    const V3<float> h = {(float)g.x, (float)g.y, (float)g.z};
+    st3(d.dvh, i, h);
+    st3(d.dvl, i, V3<float>{(float)(g.x - (double)h.x), (float)(g.y - (double)h.y), (float)(g.z - (double)h.z)});
+  } else {
+    st3(d.dv, i, g);
+  }
+}
+
+// Solve started from the guess of k_cg_guess: r = rhs - A g (the SpMV's difference form),
+// z = D^{-1} r, p_0 = z, p_{-1} = 0; partials of r.z, r.r and |rhs|^2 (the stopping test
+// stays |r| <= tol |b|).
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_cg_init_guess(Dev<R> d, const R* __restrict__ rhs) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
+    const bool on = threadIdx.x < d.work_rows[w];
+    const int i = d.work_row0[w] + threadIdx.x;
+    acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>(), v2 = acc_zero<R>();
+    if (on) {
+      spmv_row<R, false>(d, i, R(0), nullptr, d.pg);  // A g into d.Ap
+      const V3<R> b = ld3(rhs, i), ag = ld3(d.Ap, i);
+      const V3<R> r = {add_rn(b.x, -ag.x), add_rn(b.y, -ag.y), add_rn(b.z, -ag.z)};
+      const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
+      st3(d.r, i, r);
+      st3(d.z, i, z);
+      stp(d.p, i, z);                                                          // p_0 (buffer 0)
+      stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
+      v0 = acc_dot3(r, z);
+      v1 = acc_dot3(r, r);
+      v2 = acc_dot3(b, b);
+    }
+    const acc_t<R> t0 = acc_warp_total(v0), t1 = acc_warp_total(v1), t2 = acc_warp_total(v2);
+    if (lane == 0) {
+      d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
+      d.part_b[(size_t)w * kWarpsPerEntry + wp] = t1;
+      d.part_c[(size_t)w * kWarpsPerEntry + wp] = t2;
+    }
+  }
+}
+
+// End of a solve: the solution as FP64 (FP32 mode: dv = hi + lo), 0 on sheets with b = 0
+// (a solve started from a guess keeps the guess there otherwise); optionally also kept in
+// `keep` as the next solve's guess.
+template <class R>
+__global__ void k_cg_solution(Dev<R> d, double* __restrict__ keep) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.Np) return;
+  V3<double> x;
+  if constexpr (std::is_same<R, float>::value) {
+    const V3<float> h = ld3(d.dvh, i), l = ld3(d.dvl, i);
+    x = {(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z};
+  } else {
+    x = ld3(d.dv, i);
+  }
+  if (d.cg[d.vsheet[i]].zero_rhs) x = {0.0, 0.0, 0.0};
+  st3(d.dv, i, x);
+  if (keep) st3(keep, i, x);
 }
 
 template <class R>

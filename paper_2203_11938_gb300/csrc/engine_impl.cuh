@@ -144,6 +144,14 @@ class Engine final : public EngineBase {
     d.z = alloc<R>(n3, &rc);
     d.Ap = alloc<R>(n3, &rc);
     d.dv = alloc<double>(n3, &rc);
+    if (o_.cg_warm_start) {
+      // warm start: the guess in the direction layout, the forward and adjoint guess chains
+      // and the forward chain's value at every checkpoint (so a recompute replays it)
+      d.pg = alloc<R>((size_t)PStride<R>::v * L_.Np, &rc);
+      guess_f_ = alloc<double>(n3, &rc);
+      guess_a_ = alloc<double>(n3, &rc);
+      if (nseg_ > 1) ck_g_ = alloc<double>(n3 * nseg_, &rc);
+    }
     if (std::is_same<R, float>::value) {
       d.dvh = alloc<float>(n3, &rc);
       d.dvl = alloc<float>(n3, &rc);
@@ -749,7 +757,7 @@ class Engine final : public EngineBase {
         set_schedule(sched);
         k_solve_begin<R><<<1, 32, 0, st>>>(d_);
         k_cg_init<R><<<upd_grid_, kThreads, 0, st>>>(d_, d_.bvec);
-        k_cg_scalar_init<R><<<scalar_grid(), 256, 0, st>>>(d_, kPhaseForward);
+        k_cg_scalar_init<R><<<scalar_grid(), 256, 0, st>>>(d_, kPhaseForward, 0);
         emit_cg_body(st, kPhaseForward, 0, 0);  // warm-up
         CLOTH_CUDA(cudaEventRecord(ev0_, st));
         for (int k = 0; k < iters; ++k) emit_cg_body(st, kPhaseForward, 0, 0);
@@ -835,10 +843,18 @@ class Engine final : public EngineBase {
 
   // Solve A y = rhs (y left in d_.dv) for every sheet.  In graph mode the CG loop is a
   // conditional WHILE node whose condition the kernels clear when the last sheet ends.
-  int solve(const R* rhs, int phase, cudaStream_t st, bool capturing) {
+  // guess: FP64 starting vector (internal layout) or null for 0; keep: where the solution
+  // is also written (the next solve's guess) or null.
+  int solve(const R* rhs, int phase, cudaStream_t st, bool capturing, const double* guess = nullptr,
+            double* keep = nullptr) {
     launch(k_solve_begin<R>, dim3(1), dim3(32), st, d_);
-    launch(k_cg_init<R>, dim3(upd_grid_), dim3(kThreads), st, d_, rhs);
-    launch(k_cg_scalar_init<R>, dim3(scalar_grid()), dim3(256), st, d_, phase);
+    if (guess) {
+      launch(k_cg_guess<R>, dim3(grid_rows()), dim3(256), st, d_, guess);
+      launch(k_cg_init_guess<R>, dim3(upd_grid_), dim3(kThreads), st, d_, rhs);
+    } else {
+      launch(k_cg_init<R>, dim3(upd_grid_), dim3(kThreads), st, d_, rhs);
+    }
+    launch(k_cg_scalar_init<R>, dim3(scalar_grid()), dim3(256), st, d_, phase, guess ? 1 : 0);
     CLOTH_CUDA(cudaGetLastError());
     if (capturing) {
       cudaStreamCaptureStatus cs;
@@ -865,7 +881,7 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamEndCapture(body_stream_, &out));
       CLOTH_CUDA(cudaGetLastError());
       CLOTH_TRY(emit_tail(st, phase));
-      emit_solution(st);
+      emit_solution(st, guess != nullptr, keep);
       return CLOTH_OK;
     }
     const int poll = std::max(1, o_.cg_poll_every);
@@ -881,14 +897,16 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaGetLastError());
     }
     CLOTH_TRY(emit_tail(st, phase));
-    emit_solution(st);
+    emit_solution(st, guess != nullptr, keep);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
   }
 
-  // FP32 mode accumulates the solution as float-float; its consumers read FP64
-  void emit_solution(cudaStream_t st) {
-    if constexpr (std::is_same<R, float>::value) launch(k_cg_solution<R>, dim3(grid_rows()), dim3(256), st, d_);
+  // FP32 mode accumulates the solution as float-float; its consumers read FP64.  A solve
+  // from a guess also needs its b = 0 sheets set to 0, and a kept solution its copy.
+  void emit_solution(cudaStream_t st, bool guessed, double* keep) {
+    if (std::is_same<R, float>::value || guessed || keep)
+      launch(k_cg_solution<R>, dim3(grid_rows()), dim3(256), st, d_, keep);
   }
 
   // the sheets still running after the device loop finish in the per-sheet cluster
@@ -939,7 +957,7 @@ class Engine final : public EngineBase {
     elements(x, v, st);
     launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, F, v);
     CLOTH_CUDA(cudaGetLastError());
-    CLOTH_TRY(solve(d_.bvec, phase, st, cap));
+    CLOTH_TRY(solve(d_.bvec, phase, st, cap, guess_f_, guess_f_));
     launch(k_state_update<R>, dim3(grid_rows()), dim3(256), st, d_, x, v, xn, vn, traj_row);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
@@ -957,6 +975,7 @@ class Engine final : public EngineBase {
     gather_state((const R*)x0, sx(0), st);
     gather_state((const R*)v0, sv(0), st);
     launch(k_check_pins<R>, dim3(grid_rows()), dim3(256), st, d_, (const double*)sv(0));
+    if (guess_f_) CLOTH_CUDA(cudaMemsetAsync(guess_f_, 0, sizeof(double) * n3(), st));
     CLOTH_CUDA(cudaMemcpyAsync(traj_x, x0, sizeof(R) * nu3, cudaMemcpyDeviceToDevice, st));
     for (int k = 0; k < nseg_; ++k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
@@ -967,6 +986,8 @@ class Engine final : public EngineBase {
       if (nseg_ > 1) {
         CLOTH_CUDA(cudaMemcpyAsync(ck_x_ + n3() * k, sx(0), sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
         CLOTH_CUDA(cudaMemcpyAsync(ck_v_ + n3() * k, sv(0), sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
+        if (ck_g_)
+          CLOTH_CUDA(cudaMemcpyAsync(ck_g_ + n3() * k, guess_f_, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
       }
       for (int t = t0; t < t1; ++t) {
         const int j = t - t0;
@@ -988,6 +1009,7 @@ class Engine final : public EngineBase {
     CLOTH_CUDA(cudaMemsetAsync(d_.gacc_w, 0, sizeof(double) * 3 * L_.S, st));
     gather_state((const R*)dL_dx + (size_t)T_ * nu3, ax_, st);
     CLOTH_CUDA(cudaMemsetAsync(av_, 0, sizeof(double) * n3(), st));
+    if (guess_a_) CLOTH_CUDA(cudaMemsetAsync(guess_a_, 0, sizeof(double) * n3(), st));
     const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
     for (int k = nseg_ - 1; k >= 0; --k) {
       const int t0 = k * C_, t1 = std::min(T_, t0 + C_);
@@ -996,6 +1018,8 @@ class Engine final : public EngineBase {
       if (!(k == nseg_ - 1 && seg_valid == nseg_ - 1)) {
         CLOTH_CUDA(cudaMemcpyAsync(sx(0), ck_x_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
         CLOTH_CUDA(cudaMemcpyAsync(sv(0), ck_v_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
+        if (ck_g_)
+          CLOTH_CUDA(cudaMemcpyAsync(guess_f_, ck_g_ + n3() * k, sizeof(double) * n3(), cudaMemcpyDeviceToDevice, st));
         for (int t = t0; t < t1; ++t) {
           const int j = t - t0;
           CLOTH_TRY(step(sx(j), sv(j), force_row(fwd_forces_, t), sx(j + 1), sv(j + 1), nullptr, kPhaseRecompute, st,
@@ -1010,7 +1034,7 @@ class Engine final : public EngineBase {
         launch(k_assemble<R>, dim3(d_.NW), dim3(kThreads), st, d_, (const R*)nullptr, vstart);
         launch(k_adj_rhs<R>, dim3(grid_rows()), dim3(256), st, d_, (const double*)ax_, (const double*)av_);
         CLOTH_CUDA(cudaGetLastError());
-        CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap));
+        CLOTH_TRY(solve(d_.bvec, kPhaseBackward, st, cap, guess_a_, guess_a_));
         if (L_.M) launch(k_adj_tri<R>, dim3(gm), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         if (L_.E) launch(k_adj_hinge<R>, dim3(ge), dim3(kElemThreads), st, d_, (const double*)sx(j), (const double*)d_.dv, (const double*)sv(j + 1), 0);
         R* gF = g_forces ? (R*)g_forces + (size_t)t * nu3 : nullptr;
@@ -1078,6 +1102,9 @@ class Engine final : public EngineBase {
   double* vin_ = nullptr;  // a step's starting velocity v_t + F_t (velocity-increment forces)
   const R* wind_ = nullptr;  // per-sheet wind velocity [S][3] given by cloth_set_wind
   double *ax_ = nullptr, *av_ = nullptr;
+  // warm start (cloth_opts.cg_warm_start): each forward (and recomputed) solve starts from
+  // the previous step's dv, each adjoint solve from the lambda of the step after it
+  double *guess_f_ = nullptr, *guess_a_ = nullptr, *ck_g_ = nullptr;
   R *tmp_a_ = nullptr, *tmp_b_ = nullptr;
   R *mat_ = nullptr, *mat_tmp_ = nullptr;
   double* lpart_ = nullptr;

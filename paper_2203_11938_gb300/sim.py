@@ -54,6 +54,7 @@ class ClothOpts(ctypes.Structure):
         ("cg_handover", ctypes.c_int32),
         ("force_mode", ctypes.c_int32),
         ("air_density", ctypes.c_double),
+        ("cg_warm_start", ctypes.c_int32),
     ]
 
 
@@ -161,7 +162,7 @@ class ClothBatch:
 
     def __init__(self, meshes, *, steps, dt, precision="f32", cg_tol=1e-6, cg_max_iter=2000, checkpoint_every=0,
                  gravity=(0.0, 0.0, -9.8), clamp_eta=1e-3, exec_mode="graph", cg_poll_every=16, precond="block",
-                 cg_schedule=-1, cg_handover=0, force_mode="force", air_density=0.0):
+                 cg_schedule=-1, cg_handover=0, force_mode="force", air_density=0.0, cg_warm_start=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -185,6 +186,7 @@ class ClothBatch:
         o.cg_handover = int(cg_handover)
         o.force_mode = {"force": 0, "velocity": 1}[force_mode]
         o.air_density = float(air_density)
+        o.cg_warm_start = 1 if cg_warm_start else 0
         self.opts = o
         self.steps = int(steps)
         self.dtype = torch.float64 if precision == "f64" else torch.float32

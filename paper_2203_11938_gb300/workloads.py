@@ -217,3 +217,7 @@ def template_tracks(rest, steps, scale=250.0, centre=(0.5, 0.5)):
 # values: the largest grid (64 x 64) and the one the FP64 oracle needs the most CG
 # iterations for (61 x 61, the largest Y (N - 1)^2 / rho of the batch).
 BATCH_GOLDEN_SHEETS = {"largest": 93, "slowest": 220}
+
+# Solver setting of the benchmark runs (and of the full-size parity tests of the same
+# configuration): CG solves start from the previous step's solution.
+BENCH_CG_WARM_START = True

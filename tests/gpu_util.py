@@ -17,13 +17,13 @@ def to_np(t):
 
 
 def make_batch(sheets, *, steps, dt, precision, tol, max_iter=5000, ckpt=0, exec_mode="graph", eta=1e-3, poll=16,
-               precond="block", schedule=-1):
+               precond="block", schedule=-1, warm=False):
     from paper_2203_11938_gb300 import sim
 
     meshes = [(s.rest, s.tris, s.pinned) for s in sheets]
     return sim.ClothBatch(meshes, steps=steps, dt=dt, precision=precision, cg_tol=tol, cg_max_iter=max_iter,
                           checkpoint_every=ckpt, clamp_eta=eta, exec_mode=exec_mode, cg_poll_every=poll,
-                          precond=precond, cg_schedule=schedule)
+                          precond=precond, cg_schedule=schedule, cg_warm_start=warm)
 
 
 def oracle_sims(oracle, sheets):

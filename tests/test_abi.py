@@ -37,11 +37,11 @@ def test_header_declarations_are_exported(lib):
 
 def test_opts_struct_layout_matches_header(lib):
     o = sim.default_opts()
-    assert ctypes.sizeof(sim.ClothOpts) == 96  # = sizeof(cloth_opts) in C (checked with gcc)
+    assert ctypes.sizeof(sim.ClothOpts) == 104  # = sizeof(cloth_opts) in C (checked with gcc)
     assert o.precision == sim.FP32 and o.steps == 1 and o.cg_max_iter == 2000
     assert o.gravity[2] == pytest.approx(-9.8) and o.clamp_eta == pytest.approx(1e-3)
     assert o.exec == sim.EXEC_GRAPH and o.cg_poll_every == 16 and o.precond == 1 and o.cg_schedule == -1
-    assert o.cg_handover == 0 and o.force_mode == 0 and o.air_density == 0.0
+    assert o.cg_handover == 0 and o.force_mode == 0 and o.air_density == 0.0 and o.cg_warm_start == 0
 
 
 def test_mesh_create_counts(lib):

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+BENCH_WARM = W.BENCH_CG_WARM_START  # the benchmark's solver setting
 f32r = lambda a: np.asarray(a, np.float32).astype(np.float64)  # noqa: E731
 
 
@@ -73,7 +74,8 @@ def test_batch256_largest_and_slowest_sheets_match_stored_oracle():
     cfg = W.config4()
     gold = {k: _golden(f"batch_{k}") for k in W.BATCH_GOLDEN_SHEETS}
     f32 = torch.float32
-    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, max_iter=cfg.cg_max_iter)
+    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, max_iter=cfg.cg_max_iter,
+                   warm=BENCH_WARM)
     mat = np.stack([f32r(s.material) for s in cfg.sheets])
     x0 = to_cuda(np.concatenate([s.rest for s in cfg.sheets]), f32)
     traj, status = b.forward(to_cuda(mat, f32), x0, torch.zeros_like(x0), None)
@@ -103,7 +105,7 @@ def _single_sheet_case(case, cfg, steps, ckpt, loss):
     f32 = torch.float32
     assert int(g["steps"]) == steps
     b = make_batch(cfg.sheets, steps=steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, max_iter=cfg.cg_max_iter,
-                   ckpt=ckpt)
+                   ckpt=ckpt, warm=BENCH_WARM)
     x0 = to_cuda(f32r(s.rest), f32)
     F = to_cuda(f32r(s.forces[:steps]), f32)
     traj, st = b.forward(to_cuda(f32r(s.material), f32)[None], x0, torch.zeros_like(x0), F)

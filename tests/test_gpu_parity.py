@@ -282,17 +282,19 @@ def test_air_drag_matches_oracle(oracle_mod, prec):
         assert close(a, go[name], g_tol), (name, rel(a, go[name]), max_entry_err(a, go[name]))
 
 
-def test_config2_fp32_positions_and_gradients(oracle_mod):
+@pytest.mark.parametrize("warm", [False, True])
+def test_config2_fp32_positions_and_gradients(oracle_mod, warm):
     """32x32 sheet, top edge pinned, 60 steps of 1/60 s with seeded per-vertex forces,
     FP32 path (CG tol 1e-8) vs the FP64 oracle (tol 1e-10) run on the same inputs (the
     FP32 API receives x0, forces and material rounded to float; the oracle is given
     those values): max position error <= 1e-5 m, gradients w.r.t. Y, k_b, rho, forces
-    and x0 within 1e-3 relative."""
+    and x0 within 1e-3 relative.  With warm-started solves (each from the previous step's
+    solution) the same bounds hold with fewer CG iterations."""
     cfg = W.config2()
     s = cfg.sheets[0]
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
     x0, F, mat = f32(s.rest), f32(s.forces), f32(s.material)
-    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol)
+    b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, warm=warm)
     traj, status = b.forward(to_cuda(mat[None], torch.float32), to_cuda(x0, torch.float32),
                              torch.zeros(s.n, 3, dtype=torch.float32, device="cuda"), to_cuda(F, torch.float32))
     o = oracle_sims(oracle_mod, cfg.sheets)[0]
@@ -313,6 +315,11 @@ def test_config2_fp32_positions_and_gradients(oracle_mod):
     for name in ("forces", "x0"):
         a = to_np(g[name])
         assert close(a, go[name], 1e-3), (name, rel(a, go[name]), max_entry_err(a, go[name]))
+    st_ = b.stats()
+    if warm:  # the oracle solves every step from zero: the warm start must need fewer iterations
+        assert st_["fwd_cg_iters"] < 0.9 * sum(_ for _ in o.forward(mat, x0, np.zeros_like(x0), F, dt=cfg.dt,
+                                                                      steps=cfg.steps, tol=cfg.cg_tol, max_iter=20000,
+                                                                      gravity=W.GRAVITY)[2])
 
 
 def test_config2_gradients_vs_finite_differences():
@@ -404,18 +411,20 @@ def test_batched_sheets_match_their_own_oracles(oracle_mod):
             assert gm[k, q] == pytest.approx(go["material"][q], rel=1e-9)
 
 
-def test_checkpointing_and_exec_modes_agree(oracle_mod):
+@pytest.mark.parametrize("warm", [False, True])
+def test_checkpointing_and_exec_modes_agree(oracle_mod, warm):
     """Checkpoint-and-recompute (C = 3 of 10 steps), the plain host-polled CG and the CG
     kernel schedules (fused or separate direction update, resident or per-entry grid,
     with or without the per-sheet cluster solver, and the autotuned one) give bitwise the same
-    trajectory and gradients as the captured-graph run without checkpoints."""
+    trajectory and gradients as the captured-graph run without checkpoints; with
+    warm-started solves too (the recompute replays the stored starting vectors)."""
     sheets = sheets_mixed(seed=21)[:2]
     steps, dt = 10, 1 / 30
     res = []
     for exec_mode, ckpt, sched in (("graph", 0, 3), ("graph", 3, 0), ("plain", 3, 1), ("plain", 0, 2), ("graph", 0, -1),
                                    ("graph", 3, 6), ("plain", 0, 5), ("graph", 0, 4)):
         b = make_batch(sheets, steps=steps, dt=dt, precision="f32", tol=1e-6, exec_mode=exec_mode, ckpt=ckpt,
-                       schedule=sched)
+                       schedule=sched, warm=warm)
         x0 = to_cuda(np.concatenate([s.rest for s in sheets]), torch.float32)
         mat = to_cuda(_materials(sheets), torch.float32)
         traj, st = b.forward(mat, x0, torch.zeros_like(x0), None)
