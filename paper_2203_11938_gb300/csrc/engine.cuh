@@ -1297,6 +1297,226 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   }
 }
 
+// ------------------------------------------------------------------ on-chip per-sheet cluster solver
+// The same per-sheet solve as k_cg_sheet, with the sheet's data on chip: the sheet's SELL
+// slices are split into contiguous ranges, one per CTA of a thread-block cluster (up to 16
+// CTAs, one row per thread), and each CTA copies its rows' matrix values into shared
+// memory once per solve.  The vectors the SpMV gathers (z and the previous direction) live
+// in the owning CTA's shared memory and are read by the neighbours through distributed
+// shared memory, so an iteration touches neither L2 nor HBM.  Row arithmetic, per-warp
+// partial sums and the sheet-wide summation order are those of the device loop (one warp
+// per 32-row slice, the sheet's slice partials summed lane-strided then by a shuffle tree),
+// so results are bitwise the same.
+constexpr int kSmMaxRanks = 16;    // CTAs per cluster (non-portable cluster size)
+constexpr int kSmMaxThreads = 512;  // rows per CTA (keeps 128 registers per thread)
+constexpr int kSmSlots = 16;       // blocks per row the kernel keeps column addresses for
+constexpr int kSmMaxSlices = kSmMaxRanks * (kSmMaxThreads / 32);
+constexpr size_t kSmDynMax = 227 * 1024 - 1024;   // dynamic shared memory per CTA (the static part aside)
+constexpr size_t kSmBudget = kSmDynMax - 3072;      // what a partition may plan per CTA (slack for a class's
+                                                    // largest CTA against its largest row count)
+
+// Partition of one sheet: rank g holds the slices [sl0[g], sl0[g + 1]) (absolute slice ids).
+struct SmSheet {
+  int sheet;
+  int sl0[kSmMaxRanks + 1];
+};
+
+template <class R>
+__global__ void __launch_bounds__(kSmMaxThreads, 1) k_cg_sheet_sm(Dev<R> d, const SmSheet* __restrict__ list, int CL,
+                                                                  int phase) {
+  namespace cgrp = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int sl0s[kSmMaxRanks + 1];
+  __shared__ unsigned char srank[kSmMaxSlices];
+  __shared__ acc_t<R> bc_alpha;
+  __shared__ R bc_beta;
+  __shared__ int bc_stop;
+
+  const int cid = blockIdx.x / CL;
+  const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
+  const int s = list[cid].sheet;
+  if (d.cg[s].done) return;  // uniform over the cluster: written only at the end of this sheet's solve
+
+  constexpr int PS = PStride<R>::v;
+  const int MR = blockDim.x;
+  R* zs = reinterpret_cast<R*>(sm_raw);  // [MR][PS] z of this CTA's rows
+  R* pb = zs + (size_t)PS * MR;          // [2][MR][PS] directions p_k, p_{k-1} (by parity of k)
+  acc_t<R>* part = reinterpret_cast<acc_t<R>*>(pb + 2 * (size_t)PS * MR);  // [3][32] warp partials
+  R* vals = reinterpret_cast<R*>(part + 3 * 32);                          // this CTA's matrix values
+
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  if (t <= CL) sl0s[t] = list[cid].sl0[t];
+  __syncthreads();
+  const int sl_first = sl0s[0], nsl = sl0s[CL] - sl0s[0];
+  for (int q = t; q < nsl; q += MR) {
+    int g = 0;
+    while (sl0s[g + 1] <= sl_first + q) ++g;
+    srank[q] = (unsigned char)g;
+  }
+  const int sl0 = sl0s[rank], sl1 = sl0s[rank + 1];
+  const int nrows = (sl1 - sl0) * 32;
+  const bool on = t < nrows;
+  const int i = sl0 * 32 + t;
+  // this CTA's matrix values: one contiguous range of the SELL value array, 16-byte aligned
+  {
+    const int lb0 = d.slice_base[sl0];
+    const size_t n16 = ((size_t)(d.slice_base[sl1] - lb0) * 32 * 9 * sizeof(R)) / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(d.Aval + (size_t)lb0 * 32 * 9);
+    uint4* dst = reinterpret_cast<uint4*>(vals);
+    for (size_t q = t; q < n16; q += MR) dst[q] = __ldg(src + q);
+  }
+  // row state
+  int k = d.cg[s].iters;
+  R beta_r = beta_of<R>(d.cg[s]);
+  V3<R> r = {R(0), R(0), R(0)}, z = r, pold = r, Ap = r;
+  DvReg<R> x;
+  R dm[9];
+  int K = 0, lb = 0, col[kSmSlots - 1];
+  if (on) {
+    r = ld3(d.r, i);
+    z = ld3(d.z, i);
+    pold = ldp(pbuf(d, k + 1), i);
+    x.load(d, i);
+    const int sl = i >> 5;
+    K = d.slice_K[sl];
+    lb = d.slice_base[sl] - d.slice_base[sl0];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) dm[m] = d.dinv[(size_t)m * d.Np + i];
+    // column j -> (rank of its CTA) << 16 | row within that CTA
+#pragma unroll
+    for (int q = 1; q < kSmSlots; ++q) {
+      int a = 0;
+      if (q < K) {
+        const int j = d.cols[(size_t)(d.slice_base[sl] + q) * 32 + lane];
+        int g = 0;
+        while (sl0s[g + 1] * 32 <= j) ++g;
+        a = (g << 16) | (j - sl0s[g] * 32);
+      }
+      col[q - 1] = a;
+    }
+    stp(zs, t, z);
+    stp(pb + (size_t)PS * MR * ((k + 1) & 1), t, pold);
+  } else {
+#pragma unroll
+    for (int m = 0; m < 9; ++m) dm[m] = R(0);
+#pragma unroll
+    for (int q = 0; q < kSmSlots - 1; ++q) col[q] = 0;
+  }
+  const int ne8 = (d.sheet_wfirst[s + 1] - d.sheet_wfirst[s]) * kWarpsPerEntry;
+
+  auto barrier = [&]() {
+    if (CL > 1) cgrp::this_cluster().sync();
+    else __syncthreads();
+  };
+  auto remote = [&](const R* p, int g) -> const R* {
+    return CL > 1 ? cgrp::this_cluster().map_shared_rank(const_cast<R*>(p), g) : p;
+  };
+  // the sheet's sum of one partial array in the order of sheet_sum (called by one warp)
+  auto sheet_total = [&](int which) {
+    acc_t<R> acc = acc_zero<R>();
+    for (int q = lane; q < ne8; q += 32) {
+      acc_t<R> v = acc_zero<R>();
+      if (q < nsl) {
+        const int g = srank[q];
+        const acc_t<R>* src = part + which * 32 + (sl_first + q - sl0s[g]);
+        if (CL > 1) src = cgrp::this_cluster().map_shared_rank(const_cast<acc_t<R>*>(src), g);
+        v = *src;
+      }
+      acc = acc_add(acc, v);
+    }
+    return acc_warp_total(acc);
+  };
+
+  CGSheet c = d.cg[s];
+  barrier();  // every CTA's vectors are in place before the first gather
+  while (true) {
+    // ---- Ap = A p_k, p_k = z_k + beta_k p_{k-1} formed on the fly (own row and neighbours)
+    acc_t<R> vpart = acc_zero<R>();
+    V3<R> pi = {R(0), R(0), R(0)};
+    if (on) {
+      const R* pprev = pb + (size_t)PS * MR * ((k + 1) & 1);
+      pi = next_dir(z, beta_r, pold);
+      stp(pb + (size_t)PS * MR * (k & 1), t, pi);  // read by the neighbours as p_{k} next iteration
+      const R* a0 = vals + (size_t)lb * 288 + lane;
+      R ab[9];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) ab[m] = a0[32 * m];
+      V3<R> y = block_mul(ab, pi);
+#pragma unroll
+      for (int q = 1; q < kSmSlots; ++q) {
+        if (q < K) {
+          const int g = col[q - 1] >> 16, l = col[q - 1] & 0xffff;
+          const R* a = a0 + (size_t)q * 288;
+          R av[9];
+#pragma unroll
+          for (int m = 0; m < 9; ++m) av[m] = a[32 * m];
+          const V3<R> pj = next_dir(ldp(remote(zs, g), l), beta_r, ldp(remote(pprev, g), l));
+          block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
+        }
+      }
+      Ap = y;
+      vpart = acc_dot3(pi, y);
+    }
+    {
+      const acc_t<R> tw = acc_warp_total(vpart);
+      if (lane == 0) part[wp] = tw;
+    }
+    barrier();
+    if (t < 32) {
+      const acc_t<R> tsum = sheet_total(0);
+      if (t == 0) {
+        bc_stop = cg_alpha_step<R>(c, tsum);
+        bc_alpha = alpha_of<R>(c);
+      }
+    }
+    __syncthreads();
+    if (bc_stop) break;
+    // ---- dv += alpha p_k, r -= alpha Ap, z = D^{-1} r
+    acc_t<R> va = acc_zero<R>(), vb = acc_zero<R>();
+    if (on) {
+      const acc_t<R> alpha = bc_alpha;
+      x.axpy(alpha, pi);
+      const R am = -alpha_cast(alpha);
+      r = {fma_rn(am, Ap.x, r.x), fma_rn(am, Ap.y, r.y), fma_rn(am, Ap.z, r.z)};
+      z = block_mul(dm, r);  // = apply_dinv
+      stp(zs, t, z);         // gathered by the neighbours in the next iteration
+      va = acc_dot3(r, z);
+      vb = acc_dot3(r, r);
+      pold = pi;
+    }
+    {
+      const acc_t<R> ta = acc_warp_total(va), tb = acc_warp_total(vb);
+      if (lane == 0) {
+        part[32 + wp] = ta;
+        part[64 + wp] = tb;
+      }
+    }
+    barrier();
+    k += 1;
+    if (t < 32) {
+      const acc_t<R> a = sheet_total(1), b = sheet_total(2);
+      if (t == 0) {
+        bc_stop = cg_beta_step<R>(c, a, b, d.maxit);
+        bc_beta = beta_of<R>(c);
+      }
+    }
+    __syncthreads();
+    if (bc_stop) break;
+    beta_r = bc_beta;
+  }
+  if (on) {
+    x.store(d, i);
+    st3(d.r, i, r);
+    st3(d.Ap, i, Ap);
+  }
+  // no CTA leaves while another may still read its shared memory
+  barrier();
+  if (rank == 0 && t == 0) {
+    d.cg[s] = c;
+    finish_sheet(d, s, phase, 0, 0);
+  }
+}
+
 // Velocity increments: out = v + F_t on free vertices (F_t in the user layout), v elsewhere.
 template <class R>
 __global__ void k_add_increment(Dev<R> d, const double* __restrict__ v, const R* __restrict__ F,

@@ -40,6 +40,14 @@ class Engine final : public EngineBase {
     cudaEvent_t done = nullptr;
   };
 
+  // a size class of the on-chip solver: clusters of CL CTAs of MR threads, smem bytes each
+  struct SmClass {
+    int CL = 1, MR = 32, offset = 0, n = 0;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+
   // Every host-issued kernel launch goes through here so the launch count of a call
   // is known (CG loop-body kernels are counted on the device instead).
   template <class... P, class... A>
@@ -60,7 +68,12 @@ class Engine final : public EngineBase {
     if (ev0_) cudaEventDestroy(ev0_);
     if (ev1_) cudaEventDestroy(ev1_);
     if (fork_ev_) cudaEventDestroy(fork_ev_);
-    for (auto& c : classes_) {
+    for (auto* cl : {&classes_, &rest_classes_})
+      for (auto& c : *cl) {
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+      }
+    for (auto& c : sm_classes_) {
       if (c.stream) cudaStreamDestroy(c.stream);
       if (c.done) cudaEventDestroy(c.done);
     }
@@ -219,54 +232,29 @@ class Engine final : public EngineBase {
     res_spmv_[1] = resident(per_sm_f);
     res_upd_ = resident(per_sm2);
     spmv_grid_ = upd_grid_ = d.NW;
-    // per-sheet cluster solver: every sheet of at most 8 x 4 work entries (8192 rows) gets a
-    // cluster of CL CTAs with EPC entries each, CL * EPC >= its entries; sheets of a class
-    // (CL, EPC) are listed largest first, so the longest solves start first
+    // per-sheet cluster solvers: every sheet of at most 8 x 4 work entries (8192 rows) gets a
+    // cluster of CL CTAs with EPC entries each (k_cg_sheet); sheets whose rows fit the
+    // shared memory of at most 16 CTAs also get a partition for the on-chip solver
+    // (k_cg_sheet_sm)
     {
       int max_entries = 0;
       for (int s2 = 0; s2 < L_.S; ++s2) max_entries = std::max(max_entries, L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2]);
       sheet_solver_ok_ = max_entries <= 32;
       if (sheet_solver_ok_) {
-        std::map<std::pair<int, int>, std::vector<int>> cls;
-        for (int s2 = 0; s2 < L_.S; ++s2) {
-          const int E = L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2];
-          int CL = 1, EPC = 1;
-          if (E <= 1) CL = 1, EPC = 1;
-          else if (E <= 2) CL = 1, EPC = 2;
-          else if (E <= 4) CL = 2, EPC = 2;
-          else if (E <= 8) CL = 4, EPC = 2;
-          else if (E <= 16) CL = 8, EPC = 2;
-          else CL = 8, EPC = 4;
-          cls[{CL, EPC}].push_back(s2);
-        }
-        std::vector<int> lists;
-        for (auto& kv : cls) {
-          auto& v = kv.second;
-          std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
-            return L_.sheet_wfirst[a + 1] - L_.sheet_wfirst[a] > L_.sheet_wfirst[b + 1] - L_.sheet_wfirst[b];
-          });
-          SheetClass c;
-          c.CL = kv.first.first;
-          c.EPC = kv.first.second;
-          c.offset = (int)lists.size();
-          c.n = (int)v.size();
-          lists.insert(lists.end(), v.begin(), v.end());
-          if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess ||
-              cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
-            *err = "CUDA stream setup failed";
-            return CLOTH_ERR_CUDA;
-          }
-          classes_.push_back(c);
-        }
-        sheet_lists_ = upload(lists, &rc);
+        std::vector<int> all(L_.S);
+        for (int s2 = 0; s2 < L_.S; ++s2) all[s2] = s2;
+        CLOTH_TRY(make_classes(all, &classes_, &sheet_lists_, err));
+        std::vector<int> rest;
+        CLOTH_TRY(make_sm_classes(&rest, err));
+        CLOTH_TRY(make_classes(rest, &rest_classes_, &rest_lists_, err));
         // the kernel needs little shared memory: leave the rest of the SM's storage to L1,
         // which holds the matrix rows it rereads every iteration
         cudaFuncSetAttribute(k_cg_sheet<R, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         cudaFuncSetAttribute(k_cg_sheet<R, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         cudaFuncSetAttribute(k_cg_sheet<R, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
-        if (rc != CLOTH_OK || cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
           *err = "CUDA setup failed";
-          return rc != CLOTH_OK ? rc : CLOTH_ERR_CUDA;
+          return CLOTH_ERR_CUDA;
         }
       }
       cudaGetLastError();
@@ -645,11 +633,187 @@ class Engine final : public EngineBase {
     return CLOTH_OK;
   }
 
+  // Size classes (CL, EPC) of k_cg_sheet over the given sheets, each listed largest first,
+  // with a stream and an event each; the sheet lists go to the device.
+  int make_classes(const std::vector<int>& sheets, std::vector<SheetClass>* out, const int** dev_lists,
+                   std::string* err) {
+    std::map<std::pair<int, int>, std::vector<int>> cls;
+    for (int s2 : sheets) {
+      const int E = L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2];
+      int CL = 1, EPC = 1;
+      if (E <= 1) CL = 1, EPC = 1;
+      else if (E <= 2) CL = 1, EPC = 2;
+      else if (E <= 4) CL = 2, EPC = 2;
+      else if (E <= 8) CL = 4, EPC = 2;
+      else if (E <= 16) CL = 8, EPC = 2;
+      else CL = 8, EPC = 4;
+      cls[{CL, EPC}].push_back(s2);
+    }
+    std::vector<int> lists;
+    for (auto& kv : cls) {
+      auto& v = kv.second;
+      std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+        return L_.sheet_wfirst[a + 1] - L_.sheet_wfirst[a] > L_.sheet_wfirst[b + 1] - L_.sheet_wfirst[b];
+      });
+      SheetClass c;
+      c.CL = kv.first.first;
+      c.EPC = kv.first.second;
+      c.offset = (int)lists.size();
+      c.n = (int)v.size();
+      lists.insert(lists.end(), v.begin(), v.end());
+      if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
+        *err = "CUDA stream setup failed";
+        return CLOTH_ERR_CUDA;
+      }
+      out->push_back(c);
+    }
+    int rc = CLOTH_OK;
+    *dev_lists = lists.empty() ? nullptr : upload(lists, &rc);
+    if (rc != CLOTH_OK) *err = "device allocation failed";
+    return rc;
+  }
+
+  // Partitions for the on-chip solver: each sheet's slices split into the fewest contiguous
+  // ranges (CTAs, at most 16) whose matrix values and gathered vectors fit one CTA's shared
+  // memory, balanced by bytes; sheets grouped by cluster size (one launch each, largest
+  // first), each group checked to be launchable (cudaOccupancyMaxActiveClusters).  The
+  // sheets that do not fit are returned in *rest.
+  int make_sm_classes(std::vector<int>* rest, std::string* err) {
+    constexpr int PS = PStride<R>::v;
+    const size_t vec_row = 3 * PS * sizeof(R), part_bytes = 3 * 32 * sizeof(acc_t<R>);
+    const size_t budget = kSmBudget - part_bytes;
+    std::map<int, std::vector<std::pair<int, SmSheet>>> by_cl;  // CL -> (sheet, partition)
+    std::map<int, std::pair<int, size_t>> need;                 // CL -> (max rows, max value bytes)
+    for (int s2 = 0; s2 < L_.S; ++s2) {
+      const int a = L_.sheet_voff[s2] / kSlice, b = L_.sheet_voff[s2 + 1] / kSlice;
+      bool fits = true;
+      std::vector<size_t> vb(b - a);
+      size_t total = 0;
+      for (int sl = a; sl < b; ++sl) {
+        if (L_.slice_K[sl] > kSmSlots) fits = false;
+        vb[sl - a] = (size_t)L_.slice_K[sl] * 32 * 9 * sizeof(R);
+        total += vb[sl - a] + 32 * vec_row;
+      }
+      int G = 0;
+      SmSheet ps = {};
+      ps.sheet = s2;
+      size_t rows_max = 0, vals_max = 0;
+      for (int g = 1; fits && g <= kSmMaxRanks && !G; ++g) {
+        if (total > budget * g || b - a < g) continue;
+        // cut where the running byte count crosses total * k / g
+        std::vector<int> cut(g + 1, a);
+        cut[g] = b;
+        size_t run = 0;
+        int k = 1;
+        for (int sl = a; sl < b && k < g; ++sl) {
+          run += vb[sl - a] + 32 * vec_row;
+          if (run * g >= total * (size_t)k) cut[k++] = sl + 1;
+        }
+        bool ok = k == g;
+        size_t rmax = 0, vmax = 0;
+        for (int q = 0; ok && q < g; ++q) {
+          size_t v = 0;
+          for (int sl = cut[q]; sl < cut[q + 1]; ++sl) v += vb[sl - a];
+          const size_t rows = (size_t)(cut[q + 1] - cut[q]) * 32;
+          if (rows == 0 || rows > (size_t)kSmMaxThreads || v + rows * vec_row > budget) ok = false;
+          rmax = std::max(rmax, rows);
+          vmax = std::max(vmax, v);
+        }
+        if (!ok) continue;
+        G = g;
+        for (int q = 0; q <= g; ++q) ps.sl0[q] = cut[q];
+        rows_max = rmax;
+        vals_max = vmax;
+      }
+      if (!G) {
+        rest->push_back(s2);
+        continue;
+      }
+      by_cl[G].push_back({s2, ps});
+      auto& nd = need[G];
+      nd.first = std::max(nd.first, (int)rows_max);
+      nd.second = std::max(nd.second, vals_max);
+    }
+    size_t max_smem = 0;
+    bool nonportable = false;
+    for (auto& kv : need) {
+      const size_t smem = kv.second.first * vec_row + part_bytes + kv.second.second;
+      max_smem = std::max(max_smem, smem);
+      nonportable = nonportable || kv.first > 8;
+    }
+    if (by_cl.empty()) return CLOTH_OK;
+    if (cudaFuncSetAttribute(k_cg_sheet_sm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) !=
+            cudaSuccess ||
+        (nonportable && cudaFuncSetAttribute(k_cg_sheet_sm<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                            cudaSuccess)) {
+      cudaGetLastError();  // no on-chip solver on this device: every sheet to the other one
+      for (auto& kv : by_cl)
+        for (auto& e : kv.second) rest->push_back(e.first);
+      std::sort(rest->begin(), rest->end());
+      return CLOTH_OK;
+    }
+    std::vector<SmSheet> lists;
+    for (auto& kv : by_cl) {
+      const int CL = kv.first;
+      SmClass c;
+      c.CL = CL;
+      c.MR = need[CL].first;
+      c.smem = c.MR * vec_row + part_bytes + need[CL].second;
+      // launchable: at least one cluster of this shape fits the device
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3((unsigned)CL);
+      lc.blockDim = dim3((unsigned)c.MR);
+      lc.dynamicSmemBytes = c.smem;
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = (unsigned)CL;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      lc.attrs = &at;
+      lc.numAttrs = 1;
+      int nclusters = 0;
+      if (c.smem > kSmDynMax ||
+          cudaOccupancyMaxActiveClusters(&nclusters, k_cg_sheet_sm<R>, &lc) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        for (auto& e : kv.second) rest->push_back(e.first);
+        continue;
+      }
+      auto& v = kv.second;
+      std::stable_sort(v.begin(), v.end(), [&](const std::pair<int, SmSheet>& x, const std::pair<int, SmSheet>& y) {
+        return L_.sheet_voff[x.first + 1] - L_.sheet_voff[x.first] > L_.sheet_voff[y.first + 1] - L_.sheet_voff[y.first];
+      });
+      c.offset = (int)lists.size();
+      c.n = (int)v.size();
+      for (auto& e : v) lists.push_back(e.second);
+      if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
+        *err = "CUDA stream setup failed";
+        return CLOTH_ERR_CUDA;
+      }
+      sm_classes_.push_back(c);
+    }
+    std::sort(rest->begin(), rest->end());
+    if (!lists.empty()) {
+      int rc = CLOTH_OK;
+      sm_lists_ = upload(lists, &rc);
+      if (rc != CLOTH_OK) {
+        *err = "device allocation failed";
+        return rc;
+      }
+    }
+    return CLOTH_OK;
+  }
+
   // CG schedules (bitwise-identical results): bit 1 = direction update folded into the
   // SpMV (2 kernels per iteration) else a separate direction kernel (3); bit 0 = grid of
-  // resident CTAs looping over work entries else one CTA per work entry.
+  // resident CTAs looping over work entries else one CTA per work entry; bit 2 = per-sheet
+  // cluster solver after the hand-over point; bit 3 = its on-chip variant where it fits.
   void set_schedule(int sched) {
-    schedule_ = sched & 7;
+    schedule_ = sched & 15;
+    // bit 3: sheets that fit go to the on-chip per-sheet solver (reported only where it exists)
+    use_sm_ = (schedule_ & 8) != 0 && !sm_classes_.empty();
+    if (!use_sm_) schedule_ &= 7;
     sched_fused_ = (schedule_ & 2) != 0;
     spmv_grid_ = (schedule_ & 1) ? res_spmv_[sched_fused_ ? 1 : 0] : d_.NW;
     upd_grid_ = (schedule_ & 1) ? res_upd_ : d_.NW;
@@ -725,14 +889,14 @@ class Engine final : public EngineBase {
     }
     std::ostringstream key;
     key << prop.name << "|" << (sizeof(R) == 4 ? "f32" : "f64") << "|rows=" << L_.Np << "|entries=" << d_.NW
-        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover;
+        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover << "|v2";
     const std::string path = tune_cache_path();
     auto cache = path.empty() ? std::map<std::string, int>() : read_tune_cache(path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-      // value: schedule (bits 0-2) + 8 x hand-over point
-      if (o_.cg_handover == 0 && (it->second >> 3) > 0) handover_ = it->second >> 3;
-      set_schedule(it->second & 7);
+      // value: schedule (bits 0-3) + 16 x hand-over point
+      if (o_.cg_handover == 0 && (it->second >> 4) > 0) handover_ = it->second >> 4;
+      set_schedule(it->second & 15);
       return CLOTH_OK;
     }
     cudaStream_t st = cap_stream_;
@@ -786,20 +950,24 @@ class Engine final : public EngineBase {
       set_schedule(best_s);
       float t_best = 0.f;
       CLOTH_TRY(time_solve(&t_best));
-      int best_h = 0;
-      for (int p : points) {
-        handover_ = p;
-        set_schedule(best_s | 4);
-        float t = 0.f;
-        CLOTH_TRY(time_solve(&t));
-        if (t < t_best) {
-          t_best = t;
-          best_h = p;
+      int best_h = 0, best_tail = 0;
+      std::vector<int> tails = {4};
+      if (!sm_classes_.empty()) tails.push_back(12);  // the on-chip variant
+      for (int tail : tails)
+        for (int p : points) {
+          handover_ = p;
+          set_schedule(best_s | tail);
+          float t = 0.f;
+          CLOTH_TRY(time_solve(&t));
+          if (t < t_best) {
+            t_best = t;
+            best_h = p;
+            best_tail = tail;
+          }
         }
-      }
       if (best_h > 0) {
         handover_ = best_h;
-        best_s |= 4;
+        best_s |= best_tail;
       }
     }
     set_schedule(best_s);
@@ -807,7 +975,7 @@ class Engine final : public EngineBase {
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
     CLOTH_CUDA(cudaStreamSynchronize(st));
     if (!path.empty()) {
-      cache[key.str()] = best_s | ((best_s & 4) ? handover_ << 3 : 0);
+      cache[key.str()] = best_s | ((best_s & 4) ? handover_ << 4 : 0);
       write_tune_cache(path, cache);
     }
     return CLOTH_OK;
@@ -912,7 +1080,7 @@ class Engine final : public EngineBase {
   // the sheets still running after the device loop finish in the per-sheet cluster
   // solver: one launch per size class, on its own stream so the classes run side by side
   template <int EPC>
-  cudaError_t launch_class(const SheetClass& c, int phase) {
+  cudaError_t launch_class(const SheetClass& c, int phase, const int* lists) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)(c.n * c.CL));
     lc.blockDim = dim3(kThreads * EPC);
@@ -925,16 +1093,42 @@ class Engine final : public EngineBase {
     lc.attrs = &at;
     lc.numAttrs = c.CL > 1 ? 1 : 0;
     ++launches_;
-    return cudaLaunchKernelEx(&lc, k_cg_sheet<R, EPC>, d_, (const int*)(sheet_lists_ + c.offset), c.n, c.CL, phase);
+    return cudaLaunchKernelEx(&lc, k_cg_sheet<R, EPC>, d_, (const int*)(lists + c.offset), c.n, c.CL, phase);
+  }
+
+  cudaError_t launch_sm_class(const SmClass& c, int phase) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(c.n * c.CL));
+    lc.blockDim = dim3((unsigned)c.MR);
+    lc.dynamicSmemBytes = c.smem;
+    lc.stream = c.stream;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)c.CL;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    lc.attrs = &at;
+    lc.numAttrs = c.CL > 1 ? 1 : 0;
+    ++launches_;
+    return cudaLaunchKernelEx(&lc, k_cg_sheet_sm<R>, d_, (const SmSheet*)(sm_lists_ + c.offset), c.CL, phase);
   }
 
   int emit_tail(cudaStream_t st, int phase) {
     if (d_.tail_threshold <= 0) return CLOTH_OK;
     CLOTH_CUDA(cudaEventRecord(fork_ev_, st));
-    for (auto& c : classes_) {
+    if (use_sm_) {
+      for (auto& c : sm_classes_) {
+        CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
+        CLOTH_CUDA(launch_sm_class(c, phase));
+        CLOTH_CUDA(cudaEventRecord(c.done, c.stream));
+        CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
+      }
+    }
+    for (auto& c : use_sm_ ? rest_classes_ : classes_) {
       CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
-      CLOTH_CUDA(c.EPC == 1 ? launch_class<1>(c, phase) : c.EPC == 2 ? launch_class<2>(c, phase)
-                                                                      : launch_class<4>(c, phase));
+      const int* lists = use_sm_ ? rest_lists_ : sheet_lists_;
+      CLOTH_CUDA(c.EPC == 1 ? launch_class<1>(c, phase, lists) : c.EPC == 2 ? launch_class<2>(c, phase, lists)
+                                                                             : launch_class<4>(c, phase, lists));
       CLOTH_CUDA(cudaEventRecord(c.done, c.stream));
       CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
     }
@@ -1115,6 +1309,13 @@ class Engine final : public EngineBase {
   int spmv_grid_ = 1, upd_grid_ = 1;  // CTAs of the SpMV and of the other CG row kernels
   std::vector<SheetClass> classes_;  // size classes of the per-sheet cluster solver
   const int* sheet_lists_ = nullptr;  // their sheets, class after class
+  // on-chip solver: its size classes (one cluster size each), their partitions, and the
+  // k_cg_sheet classes of the sheets it cannot hold
+  std::vector<SmClass> sm_classes_;
+  const SmSheet* sm_lists_ = nullptr;
+  std::vector<SheetClass> rest_classes_;
+  const int* rest_lists_ = nullptr;
+  bool use_sm_ = false;
   bool sheet_solver_ok_ = false;      // every sheet fits one cluster
   int handover_ = 1 << 30;            // sheets left when the device loop hands over
   cudaEvent_t fork_ev_ = nullptr;

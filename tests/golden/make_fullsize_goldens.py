@@ -15,9 +15,10 @@ FP32 path receives them, and stores the values the GPU tests compare entry by en
       segment) with the smooth wind; loss = pinhole reprojection against the template's
       tracks (workloads.template_tracks); oracle CG tol 1e-9.
   grid256_segment
-      the 256 x 256 sheet with four corners pinned, its first 20 steps (one checkpoint
-      segment) with the smooth wind; loss L = sum_{t>=1} |x_t - X|^2; oracle CG tol 1e-9.
-      Per-vertex arrays are stored for every 5th vertex (all norms are of the full arrays).
+      the 256 x 256 sheet with four corners pinned, its first 4 steps with the smooth wind
+      (the oracle needs about 20 minutes per solve at this size); loss
+      L = sum_{t>=1} |x_t - X|^2; oracle CG tol 1e-8.  Per-vertex arrays are stored for
+      every 5th vertex (all norms are of the full arrays).
 
 Run: python tests/golden/make_fullsize_goldens.py [case ...]   (hours of CPU time; each
 case runs in its own process, all cases in parallel).
@@ -37,6 +38,10 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 CASES = ("batch_largest", "batch_slowest", "grid100_segment", "grid256_segment")
+# The oracle's map-per-row sparse matrix needs about 20 minutes per solve of the 65,536-vertex
+# sheet, so its stored run covers the first 4 steps (forward and adjoint), not a whole
+# 20-step checkpoint segment.
+GRID256_STEPS = 4
 
 
 def f32r(a):
@@ -57,9 +62,10 @@ def _case_inputs(case):
         return dict(sheet=s, index=0, steps=30, dt=cfg.dt, forces=s.forces[:30], loss="pinhole", tol=1e-9,
                     stride=1, camera=cfg.camera)
     if case == "grid256_segment":
-        cfg = W.config5(steps=20)
+        cfg = W.config5(steps=GRID256_STEPS)
         s = cfg.sheets[0]
-        return dict(sheet=s, index=0, steps=20, dt=cfg.dt, forces=s.forces[:20], loss="l2", tol=1e-9, stride=5)
+        return dict(sheet=s, index=0, steps=GRID256_STEPS, dt=cfg.dt, forces=s.forces[:GRID256_STEPS], loss="l2",
+                    tol=1e-8, stride=5)
     raise ValueError(case)
 
 

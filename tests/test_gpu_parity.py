@@ -442,10 +442,12 @@ def test_checkpointing_and_exec_modes_agree(oracle_mod, warm):
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_sheet_solver_matches_device_loop_bitwise(precision):
-    """The per-sheet cluster solver (schedule bit 2) against the device loop alone, on
-    sheets of 1 to 20 work entries (every cluster size and entries-per-CTA class): bitwise
-    the same trajectory, gradients and per-sheet iteration counts, in graph and plain
-    execution."""
+    """The per-sheet cluster solver (schedule bit 2) and its on-chip variant (bit 3: matrix
+    and gathered vectors in the shared memory of up to 16 CTAs, neighbours read through
+    distributed shared memory) against the device loop alone, on sheets of 1 to 20 work
+    entries (every cluster size and entries-per-CTA class; in FP64 the largest sheets do
+    not fit on chip and take the first solver): bitwise the same trajectory, gradients and
+    per-sheet iteration counts, in graph and plain execution."""
     rng = np.random.Generator(np.random.PCG64(8))
     sheets = []
     for N in (16, 20, 30, 40, 50, 64, 70):
@@ -453,9 +455,9 @@ def test_sheet_solver_matches_device_loop_bitwise(precision):
         sheets.append(W.Sheet(N, rest, tris, W.pins(N, "top2"), W.sample_material(rng), None))
     dtype = torch.float32 if precision == "f32" else torch.float64
     res = []
-    for exec_mode, sched in (("graph", 2), ("graph", 6), ("plain", 7)):
+    for exec_mode, sched in (("graph", 2), ("graph", 6), ("plain", 7), ("graph", 14), ("plain", 15)):
         b = make_batch(sheets, steps=4, dt=1 / 30, precision=precision, tol=1e-7, exec_mode=exec_mode, schedule=sched)
-        assert b.matrix_info()["cg_schedule"] == sched
+        assert b.matrix_info()["cg_schedule"] == sched  # bit 3: the on-chip solver holds at least one sheet
         x0 = to_cuda(np.concatenate([s.rest for s in sheets]), dtype)
         mat = to_cuda(_materials(sheets), dtype)
         traj, st = b.forward(mat, x0, torch.zeros_like(x0), None)
