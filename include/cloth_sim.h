@@ -95,14 +95,17 @@ typedef struct cloth_opts {
                                -1 = autotune at cloth_batch_create (times each schedule
                                on the batch's matrix, caches the choice in the JSON file
                                $CLOTH_TUNE_CACHE or ~/.cache/cloth_sim/tune.json);
-                               0..15: bit 1 = direction update folded into the SpMV,
+                               0..31: bit 1 = direction update folded into the SpMV,
                                bit 0 = resident-CTA grid looping over rows, bit 2 =
                                per-sheet cluster solver for the sheets still iterating
                                at the hand-over point (every sheet of at most 8192
                                vertices gets one thread-block cluster), bit 3 (with
                                bit 2) = the on-chip variant of that solver for every
                                sheet whose matrix and vectors fit the shared memory of
-                               at most 16 CTAs (the others keep the first variant)    */
+                               at most 16 CTAs (the others keep the first variant),
+                               bit 4 (with bit 2, without bit 3) = that solver with one
+                               256-row work entry per CTA, clusters of up to 16 CTAs
+                               and three CTAs per SM                                  */
   int32_t cg_handover;      /* with schedule bit 2: the device loop runs while more than
                                this many sheets are still iterating, then the per-sheet
                                solver finishes them (>= count: no loop at all);
@@ -222,7 +225,7 @@ int cloth_sheet_iterations(cloth_batch* batch, int32_t phase, int32_t* max_iters
 /* Size of the step matrix A (Eq. 4-5) in 3x3 blocks: rows (vertices, each sheet
  * padded to a multiple of 32), blocks (structurally nonzero blocks) and
  * stored_blocks (blocks stored by the SELL-32 layout, padding included); cg_schedule:
- * the CG kernel schedule in use (0..15, see cloth_opts).  Any pointer may be NULL. */
+ * the CG kernel schedule in use (0..31, see cloth_opts).  Any pointer may be NULL. */
 int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks,
                       int64_t* stored_blocks, int32_t* cg_schedule);
 

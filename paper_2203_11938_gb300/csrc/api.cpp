@@ -96,7 +96,7 @@ int cloth_batch_create(const cloth_mesh* const* meshes, int32_t count, const clo
   if (o.steps < 1 || !(o.dt > 0.0) || !(o.cg_tol >= 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 ||
       !(o.clamp_eta >= 0.0) || (o.exec != CLOTH_EXEC_PLAIN && o.exec != CLOTH_EXEC_GRAPH) || o.cg_poll_every < 1 ||
       (o.precond != CLOTH_PRECOND_JACOBI && o.precond != CLOTH_PRECOND_BLOCK_JACOBI) || o.cg_schedule < -1 ||
-      o.cg_schedule > 15 || o.cg_handover < 0 ||
+      o.cg_schedule > 31 || o.cg_handover < 0 ||
       (o.force_mode != CLOTH_FORCES_FORCE && o.force_mode != CLOTH_FORCES_VELOCITY) ||
       !(o.air_density >= 0.0) || (o.cg_warm_start != 0 && o.cg_warm_start != 1))
     return fail(CLOTH_ERR_INVALID_ARG, "cloth_batch_create: invalid option value");

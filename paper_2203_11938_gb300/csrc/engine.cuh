@@ -1133,9 +1133,12 @@ template <> __device__ __forceinline__ V3<float> ldp_l2<float>(const float* a, i
   return {q.x, q.y, q.z};
 }
 
-template <class R, int EPC>
-__global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(Dev<R> d, const int* __restrict__ sheets, int nsheets,
-                                                             int CL, int phase) {
+// MINB: CTAs per SM the register budget is sized for (3 for the dense one-entry classes,
+// which put several sheets' CTAs on each SM so that one sheet's barrier waits overlap
+// another's work).
+template <class R, int EPC, int MINB = (EPC == 1 ? 2 : 1)>
+__global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, const int* __restrict__ sheets, int nsheets,
+                                                                   int CL, int phase) {
   namespace cgrp = cooperative_groups;
   const int cid = blockIdx.x / CL;
   const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
@@ -1162,16 +1165,40 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   };
   // the sheet's sum of one partial array, in the order of sheet_sum (lane-strided, then a
   // shuffle tree); called by one full warp
-  auto sheet_total = [&](int which) {
-    acc_t<R> acc = acc_zero<R>();
-    for (int q = w0 * kWarpsPerEntry + lane; q < w1 * kWarpsPerEntry; q += 32) {
-      const int e = q / kWarpsPerEntry - w0, pw = q % kWarpsPerEntry;
-      const int rk = e % CL, jj = e / CL;
-      const acc_t<R>* src = &sp[which][jj][pw];
-      if (CL > 1) src = cgrp::this_cluster().map_shared_rank(src, rk);
-      acc = acc_add(acc, *src);
+  // The sheet's sums of one or two partial arrays, each in the order of sheet_sum
+  // (lane-strided, then a shuffle tree); every partial is loaded before the first add, so
+  // the (distributed) shared memory loads overlap.  Called by one full warp.
+  constexpr int kPerLane = EPC == 4 ? 8 : 4;  // partials per lane: a class holds at most 16 (EPC <= 2) or 32 entries
+  auto sheet_totals = [&](int wa, int wb, acc_t<R>* ta, acc_t<R>* tb) {
+    acc_t<R> va[kPerLane], vb[kPerLane];
+    const int q0 = w0 * kWarpsPerEntry, q1 = w1 * kWarpsPerEntry;
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+      const int q = q0 + lane + 32 * u;
+      va[u] = acc_zero<R>();
+      vb[u] = acc_zero<R>();
+      if (q < q1) {
+        const int e = q / kWarpsPerEntry - w0, pw = q % kWarpsPerEntry;
+        const int rk = e % CL, jj = e / CL;
+        const acc_t<R>* sa = &sp[wa][jj][pw];
+        const acc_t<R>* sb = &sp[wb][jj][pw];
+        if (CL > 1) {
+          sa = cgrp::this_cluster().map_shared_rank(sa, rk);
+          sb = cgrp::this_cluster().map_shared_rank(sb, rk);
+        }
+        va[u] = *sa;
+        if (tb) vb[u] = *sb;
+      }
     }
-    return acc_warp_total(acc);
+    acc_t<R> a = acc_zero<R>(), b = acc_zero<R>();
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u)
+      if (q0 + lane + 32 * u < q1) {
+        a = acc_add(a, va[u]);
+        b = acc_add(b, vb[u]);
+      }
+    *ta = acc_warp_total(a);
+    if (tb) *tb = acc_warp_total(b);
   };
 
   // row state
@@ -1192,8 +1219,10 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
   }
 #pragma unroll
   for (int q = 0; q < kColCache; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
-  // thread 0's copy of the sheet's scalars, advanced by the loop's scalar steps
-  CGSheet c = d.cg[s];
+  // the sheet's scalars, advanced by thread 0 with the loop's scalar steps (in shared memory:
+  // a register copy in every thread would cost ~26 registers per thread)
+  __shared__ CGSheet c;
+  if (threadIdx.x == 0) c = d.cg[s];
 
   while (true) {
     // ---- Ap = A p_k, p_k = z_k + beta_k p_{k-1} formed on the fly (own row and neighbours)
@@ -1238,7 +1267,8 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
     }
     barrier();
     if (threadIdx.x < 32) {
-      const acc_t<R> tsum = sheet_total(0);
+      acc_t<R> tsum;
+      sheet_totals(0, 0, &tsum, nullptr);
       if (threadIdx.x == 0) {
         bc_stop = cg_alpha_step<R>(c, tsum);
         bc_alpha = alpha_of<R>(c);
@@ -1274,7 +1304,8 @@ __global__ void __launch_bounds__(kThreads * EPC, EPC == 1 ? 2 : 1) k_cg_sheet(D
     barrier();
     k += 1;
     if (threadIdx.x < 32) {
-      const acc_t<R> a = sheet_total(1), b = sheet_total(2);
+      acc_t<R> a, b;
+      sheet_totals(1, 2, &a, &b);
       if (threadIdx.x == 0) {
         bc_stop = cg_beta_step<R>(c, a, b, d.maxit);
         bc_beta = beta_of<R>(c);
@@ -1412,22 +1443,40 @@ __global__ void __launch_bounds__(kSmMaxThreads, 1) k_cg_sheet_sm(Dev<R> d, cons
     return CL > 1 ? cgrp::this_cluster().map_shared_rank(const_cast<R*>(p), g) : p;
   };
   // the sheet's sum of one partial array in the order of sheet_sum (called by one warp)
-  auto sheet_total = [&](int which) {
-    acc_t<R> acc = acc_zero<R>();
-    for (int q = lane; q < ne8; q += 32) {
-      acc_t<R> v = acc_zero<R>();
+  // (two totals at once; every partial loaded before the first add, as in k_cg_sheet)
+  constexpr int kPerLane = kSmMaxSlices / 32;
+  auto sheet_totals = [&](int wa, int wb, acc_t<R>* ta, acc_t<R>* tb) {
+    acc_t<R> va[kPerLane], vb[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+      const int q = lane + 32 * u;
+      va[u] = acc_zero<R>();
+      vb[u] = acc_zero<R>();
       if (q < nsl) {
         const int g = srank[q];
-        const acc_t<R>* src = part + which * 32 + (sl_first + q - sl0s[g]);
-        if (CL > 1) src = cgrp::this_cluster().map_shared_rank(const_cast<acc_t<R>*>(src), g);
-        v = *src;
+        const acc_t<R>* sa = part + wa * 32 + (sl_first + q - sl0s[g]);
+        const acc_t<R>* sb = part + wb * 32 + (sl_first + q - sl0s[g]);
+        if (CL > 1) {
+          sa = cgrp::this_cluster().map_shared_rank(const_cast<acc_t<R>*>(sa), g);
+          sb = cgrp::this_cluster().map_shared_rank(const_cast<acc_t<R>*>(sb), g);
+        }
+        va[u] = *sa;
+        if (tb) vb[u] = *sb;
       }
-      acc = acc_add(acc, v);
     }
-    return acc_warp_total(acc);
+    acc_t<R> a = acc_zero<R>(), b = acc_zero<R>();
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u)
+      if (lane + 32 * u < ne8) {
+        a = acc_add(a, va[u]);
+        b = acc_add(b, vb[u]);
+      }
+    *ta = acc_warp_total(a);
+    if (tb) *tb = acc_warp_total(b);
   };
 
-  CGSheet c = d.cg[s];
+  __shared__ CGSheet c;  // advanced by thread 0 (see k_cg_sheet)
+  if (t == 0) c = d.cg[s];
   barrier();  // every CTA's vectors are in place before the first gather
   while (true) {
     // ---- Ap = A p_k, p_k = z_k + beta_k p_{k-1} formed on the fly (own row and neighbours)
@@ -1463,7 +1512,8 @@ __global__ void __launch_bounds__(kSmMaxThreads, 1) k_cg_sheet_sm(Dev<R> d, cons
     }
     barrier();
     if (t < 32) {
-      const acc_t<R> tsum = sheet_total(0);
+      acc_t<R> tsum;
+      sheet_totals(0, 0, &tsum, nullptr);
       if (t == 0) {
         bc_stop = cg_alpha_step<R>(c, tsum);
         bc_alpha = alpha_of<R>(c);
@@ -1494,7 +1544,8 @@ __global__ void __launch_bounds__(kSmMaxThreads, 1) k_cg_sheet_sm(Dev<R> d, cons
     barrier();
     k += 1;
     if (t < 32) {
-      const acc_t<R> a = sheet_total(1), b = sheet_total(2);
+      acc_t<R> a, b;
+      sheet_totals(1, 2, &a, &b);
       if (t == 0) {
         bc_stop = cg_beta_step<R>(c, a, b, d.maxit);
         bc_beta = beta_of<R>(c);

@@ -36,6 +36,7 @@ class Engine final : public EngineBase {
   // a size class of the per-sheet cluster solver: CL CTAs per cluster, EPC work entries per CTA
   struct SheetClass {
     int CL = 1, EPC = 1, offset = 0, n = 0;
+    bool dense = false;  // k_cg_sheet<R, 1, 3>: several CTAs per SM
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
   };
@@ -68,7 +69,7 @@ class Engine final : public EngineBase {
     if (ev0_) cudaEventDestroy(ev0_);
     if (ev1_) cudaEventDestroy(ev1_);
     if (fork_ev_) cudaEventDestroy(fork_ev_);
-    for (auto* cl : {&classes_, &rest_classes_})
+    for (auto* cl : {&classes_, &rest_classes_, &dense_classes_})
       for (auto& c : *cl) {
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
@@ -247,6 +248,7 @@ class Engine final : public EngineBase {
         std::vector<int> rest;
         CLOTH_TRY(make_sm_classes(&rest, err));
         CLOTH_TRY(make_classes(rest, &rest_classes_, &rest_lists_, err));
+        CLOTH_TRY(make_dense_classes(all, err));
         // the kernel needs little shared memory: leave the rest of the SM's storage to L1,
         // which holds the matrix rows it rereads every iteration
         cudaFuncSetAttribute(k_cg_sheet<R, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
@@ -635,13 +637,16 @@ class Engine final : public EngineBase {
 
   // Size classes (CL, EPC) of k_cg_sheet over the given sheets, each listed largest first,
   // with a stream and an event each; the sheet lists go to the device.
+  // dense: one work entry per CTA (cluster of E CTAs for a sheet of E <= 16 entries, three
+  // CTAs per SM); sheets of more entries take the (8, 4) class.
   int make_classes(const std::vector<int>& sheets, std::vector<SheetClass>* out, const int** dev_lists,
-                   std::string* err) {
+                   std::string* err, bool dense = false) {
     std::map<std::pair<int, int>, std::vector<int>> cls;
     for (int s2 : sheets) {
       const int E = L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2];
       int CL = 1, EPC = 1;
-      if (E <= 1) CL = 1, EPC = 1;
+      if (dense && E <= 16) CL = E, EPC = 1;
+      else if (E <= 1) CL = 1, EPC = 1;
       else if (E <= 2) CL = 1, EPC = 2;
       else if (E <= 4) CL = 2, EPC = 2;
       else if (E <= 8) CL = 4, EPC = 2;
@@ -658,6 +663,7 @@ class Engine final : public EngineBase {
       SheetClass c;
       c.CL = kv.first.first;
       c.EPC = kv.first.second;
+      c.dense = dense && c.EPC == 1;
       c.offset = (int)lists.size();
       c.n = (int)v.size();
       lists.insert(lists.end(), v.begin(), v.end());
@@ -672,6 +678,37 @@ class Engine final : public EngineBase {
     *dev_lists = lists.empty() ? nullptr : upload(lists, &rc);
     if (rc != CLOTH_OK) *err = "device allocation failed";
     return rc;
+  }
+
+  // Dense classes (schedule bit 4), kept only if every cluster shape can be launched.
+  int make_dense_classes(const std::vector<int>& all, std::string* err) {
+    std::vector<SheetClass> cl;
+    const int* lists = nullptr;
+    CLOTH_TRY(make_classes(all, &cl, &lists, err, true));
+    bool ok = cudaFuncSetAttribute(k_cg_sheet<R, 1, 3>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+              cudaSuccess;
+    cudaFuncSetAttribute(k_cg_sheet<R, 1, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxL1);
+    for (const auto& c : cl) {
+      if (!ok || !c.dense) continue;
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3((unsigned)c.CL);
+      lc.blockDim = dim3(kThreads);
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = (unsigned)c.CL;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      lc.attrs = &at;
+      lc.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_cg_sheet<R, 1, 3>, &lc) != cudaSuccess || n < 1) ok = false;
+    }
+    cudaGetLastError();
+    dense_classes_ = cl;  // destroyed with the engine either way
+    dense_lists_ = lists;
+    dense_ok_ = ok;
+    return CLOTH_OK;
   }
 
   // Partitions for the on-chip solver: each sheet's slices split into the fewest contiguous
@@ -810,10 +847,13 @@ class Engine final : public EngineBase {
   // resident CTAs looping over work entries else one CTA per work entry; bit 2 = per-sheet
   // cluster solver after the hand-over point; bit 3 = its on-chip variant where it fits.
   void set_schedule(int sched) {
-    schedule_ = sched & 15;
-    // bit 3: sheets that fit go to the on-chip per-sheet solver (reported only where it exists)
+    schedule_ = sched & 31;
+    // bit 3: sheets that fit go to the on-chip per-sheet solver; bit 4: the dense classes of
+    // the per-sheet solver (each reported only where it exists)
     use_sm_ = (schedule_ & 8) != 0 && !sm_classes_.empty();
-    if (!use_sm_) schedule_ &= 7;
+    use_dense_ = (schedule_ & 16) != 0 && !use_sm_ && dense_ok_;
+    if (!use_sm_) schedule_ &= ~8;
+    if (!use_dense_) schedule_ &= ~16;
     sched_fused_ = (schedule_ & 2) != 0;
     spmv_grid_ = (schedule_ & 1) ? res_spmv_[sched_fused_ ? 1 : 0] : d_.NW;
     upd_grid_ = (schedule_ & 1) ? res_upd_ : d_.NW;
@@ -889,14 +929,14 @@ class Engine final : public EngineBase {
     }
     std::ostringstream key;
     key << prop.name << "|" << (sizeof(R) == 4 ? "f32" : "f64") << "|rows=" << L_.Np << "|entries=" << d_.NW
-        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover << "|v2";
+        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover << "|v3";
     const std::string path = tune_cache_path();
     auto cache = path.empty() ? std::map<std::string, int>() : read_tune_cache(path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-      // value: schedule (bits 0-3) + 16 x hand-over point
-      if (o_.cg_handover == 0 && (it->second >> 4) > 0) handover_ = it->second >> 4;
-      set_schedule(it->second & 15);
+      // value: schedule (bits 0-4) + 32 x hand-over point
+      if (o_.cg_handover == 0 && (it->second >> 5) > 0) handover_ = it->second >> 5;
+      set_schedule(it->second & 31);
       return CLOTH_OK;
     }
     cudaStream_t st = cap_stream_;
@@ -953,6 +993,7 @@ class Engine final : public EngineBase {
       int best_h = 0, best_tail = 0;
       std::vector<int> tails = {4};
       if (!sm_classes_.empty()) tails.push_back(12);  // the on-chip variant
+      if (dense_ok_) tails.push_back(20);             // the dense classes
       for (int tail : tails)
         for (int p : points) {
           handover_ = p;
@@ -975,7 +1016,7 @@ class Engine final : public EngineBase {
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
     CLOTH_CUDA(cudaStreamSynchronize(st));
     if (!path.empty()) {
-      cache[key.str()] = best_s | ((best_s & 4) ? handover_ << 4 : 0);
+      cache[key.str()] = best_s | ((best_s & 4) ? handover_ << 5 : 0);
       write_tune_cache(path, cache);
     }
     return CLOTH_OK;
@@ -1079,7 +1120,7 @@ class Engine final : public EngineBase {
 
   // the sheets still running after the device loop finish in the per-sheet cluster
   // solver: one launch per size class, on its own stream so the classes run side by side
-  template <int EPC>
+  template <int EPC, int MINB = (EPC == 1 ? 2 : 1)>
   cudaError_t launch_class(const SheetClass& c, int phase, const int* lists) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)(c.n * c.CL));
@@ -1093,7 +1134,7 @@ class Engine final : public EngineBase {
     lc.attrs = &at;
     lc.numAttrs = c.CL > 1 ? 1 : 0;
     ++launches_;
-    return cudaLaunchKernelEx(&lc, k_cg_sheet<R, EPC>, d_, (const int*)(lists + c.offset), c.n, c.CL, phase);
+    return cudaLaunchKernelEx(&lc, k_cg_sheet<R, EPC, MINB>, d_, (const int*)(lists + c.offset), c.n, c.CL, phase);
   }
 
   cudaError_t launch_sm_class(const SmClass& c, int phase) {
@@ -1124,11 +1165,14 @@ class Engine final : public EngineBase {
         CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
       }
     }
-    for (auto& c : use_sm_ ? rest_classes_ : classes_) {
+    auto& set = use_sm_ ? rest_classes_ : use_dense_ ? dense_classes_ : classes_;
+    const int* lists = use_sm_ ? rest_lists_ : use_dense_ ? dense_lists_ : sheet_lists_;
+    for (auto& c : set) {
       CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
-      const int* lists = use_sm_ ? rest_lists_ : sheet_lists_;
-      CLOTH_CUDA(c.EPC == 1 ? launch_class<1>(c, phase, lists) : c.EPC == 2 ? launch_class<2>(c, phase, lists)
-                                                                             : launch_class<4>(c, phase, lists));
+      const cudaError_t le = c.dense ? launch_class<1, 3>(c, phase, lists)
+                             : c.EPC == 1 ? launch_class<1>(c, phase, lists)
+                             : c.EPC == 2 ? launch_class<2>(c, phase, lists) : launch_class<4>(c, phase, lists);
+      CLOTH_CUDA(le);
       CLOTH_CUDA(cudaEventRecord(c.done, c.stream));
       CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
     }
@@ -1316,6 +1360,9 @@ class Engine final : public EngineBase {
   std::vector<SheetClass> rest_classes_;
   const int* rest_lists_ = nullptr;
   bool use_sm_ = false;
+  std::vector<SheetClass> dense_classes_;  // schedule bit 4
+  const int* dense_lists_ = nullptr;
+  bool dense_ok_ = false, use_dense_ = false;
   bool sheet_solver_ok_ = false;      // every sheet fits one cluster
   int handover_ = 1 << 30;            // sheets left when the device loop hands over
   cudaEvent_t fork_ev_ = nullptr;

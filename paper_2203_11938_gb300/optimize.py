@@ -111,6 +111,7 @@ class FitResult:
     forces: np.ndarray         # [T, N, 3]
     history: list              # per iteration: (active frames, energy of the active frames)
     window: AdaptiveWindow
+    materials: list = field(default_factory=list)  # per iteration: the material [S, 4] it simulated
 
 
 def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr=1e-3, first=5, max_iters=50,
@@ -119,7 +120,9 @@ def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr
     the adaptive window.  batch: a sim.ClothBatch; material0 [S, 4], x0/v0 [N, 3],
     tracks [T+1, N, 2] (device tensors of the batch's precision) for the pinhole-track
     loss, or frame_loss(traj) -> (per-frame energies [T+1], dL/dx [T+1, N, 3]) in its
-    place (e.g. image_frame_loss; tracks and camera are then unused)."""
+    place (e.g. image_frame_loss; tracks and camera are then unused).  batch may be any
+    object with the same steps, forward, loss_pinhole and backward (the tests drive the
+    same schedule through the oracle that way)."""
     import torch
 
     dtype = x0.dtype
@@ -131,7 +134,7 @@ def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr
     params = [logm] + ([F] if optimise_forces else [])
     opt = torch.optim.Adam(params, lr=lr)
     window = AdaptiveWindow(T, first=first, max_iters=max_iters)
-    history = []
+    history, materials = [], []
     # fixed input buffers: the library caches one captured graph per set of argument addresses
     mat = torch.empty(material0.shape, dtype=dtype, device=x0.device)
     Fc = torch.empty(T, x0.shape[0], 3, dtype=dtype, device=x0.device)
@@ -148,6 +151,7 @@ def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr
         dL[window.active + 1:] = 0  # frames after the active one do not take part
         g = batch.backward(dL)
         history.append((window.active, float(e[1:window.active + 1].sum())))
+        materials.append(mat.detach().double().cpu().numpy().copy())
         opt.zero_grad()
         gm = g["material"].double()
         logm.grad = torch.stack([gm[:, 0], gm[:, 2], gm[:, 3]], dim=1) * m  # chain rule through exp
@@ -157,4 +161,4 @@ def fit(batch, material0, x0, v0, tracks, camera, *, forces0=None, iters=200, lr
         window.step(np.asarray(e.detach().cpu() if hasattr(e, "cpu") else e, dtype=np.float64))
     m = torch.exp(logm.detach())
     mat = torch.stack([m[:, 0], nu.double(), m[:, 1], m[:, 2]], dim=1)
-    return FitResult(mat.cpu().numpy(), F.detach().cpu().numpy(), history, window)
+    return FitResult(mat.cpu().numpy(), F.detach().cpu().numpy(), history, window, materials)

@@ -81,7 +81,7 @@ def test_batch_create_rejects_bad_options_on_host(lib):
     h = ctypes.c_void_p()
     for field, value in (("steps", 0), ("dt", -1.0), ("cg_max_iter", 0), ("precision", 7), ("exec", 9),
                          ("clamp_eta", -1.0), ("cg_poll_every", 0), ("precond", 5),
-                         ("cg_schedule", 16), ("cg_schedule", -2), ("cg_handover", -1),
+                         ("cg_schedule", 32), ("cg_schedule", -2), ("cg_handover", -1),
                          ("force_mode", 2), ("air_density", -1.0), ("cg_warm_start", 2)):
         o = sim.default_opts()
         setattr(o, field, value)
