@@ -20,7 +20,9 @@ sigma = 7 px and lambda = 0.5; the rasteriser's own constants are readings):
   triangle), blended with weights w_j = D_j exp(zn_j / GAMMA) against a black background
   of weight exp(EPS / GAMMA), where zn_j is the normalised inverse depth at p
   (1 nearest at Z_NEAR, 0 at Z_FAR), interpolated with the same barycentric coordinates;
-  the exponentials are evaluated relative to the largest exponent (a stable softmax);
+  the weights are evaluated as exp(zn_j / GAMMA + log D_j - top) with top the largest of
+  these exponents and EPS / GAMMA (a stable softmax that keeps the background's weight at
+  pixels where every D_j underflows);
 * E_p = sum_p sum_rgb |I(p) - I_hat(p)|;  E_s = sum_p |G(A)(p) - G(B_hat)(p)| with G the
   Gaussian filter of standard deviation SIGMA_S px (truncated at 3 sigma, zero outside the
   image); the energy of a frame is E_p + LAMBDA E_s.
@@ -79,19 +81,20 @@ def _barycentric(p, a, b, c):
 
 
 def coverage(q, tris, W, H):
-    """Coverage probabilities D [m, H, W], barycentric coordinates [m, H, W, 3] of every
-    pixel centre in every projected triangle (q: image points [n, 2])."""
+    """Signed sigmoid arguments s = +-d^2 / SIGMA_R [m, H, W] (coverage D = sigmoid(s)) and
+    barycentric coordinates [m, H, W, 3] of every pixel centre in every projected triangle
+    (q: image points [n, 2])."""
     P = pixel_centres(W, H)
-    D, L = [], []
+    S, L = [], []
     for (i, j, k) in tris:
         a, b, c = q[i], q[j], q[k]
         lam = _barycentric(P, a, b, c)
         inside = (lam >= 0).all(-1)
         d2 = torch.minimum(torch.minimum(_segment_distance2(P, a, b), _segment_distance2(P, b, c)),
                            _segment_distance2(P, c, a))
-        D.append(torch.sigmoid(torch.where(inside, d2, -d2) / SIGMA_R))
+        S.append(torch.where(inside, d2, -d2) / SIGMA_R)
         L.append(lam)
-    return torch.stack(D), torch.stack(L)
+    return torch.stack(S), torch.stack(L)
 
 
 def silhouette(D):
@@ -119,7 +122,8 @@ def render(x, tris, uv, tex, camera, W, H):
     with per-vertex texture coordinates uv [n, 2] and texture tex [Ht, Wt, 3]."""
     x, uv, tex = _t(x), _t(uv), _t(tex)
     q, depth = project(x, camera, W, H)
-    D, L = coverage(q, tris, W, H)
+    Sarg, L = coverage(q, tris, W, H)
+    D = torch.sigmoid(Sarg)
     Lc = L.clamp(min=0.0)
     Lc = Lc / Lc.sum(-1, keepdim=True)
     tri = torch.as_tensor(np.asarray(tris, np.int64))
@@ -127,9 +131,13 @@ def render(x, tris, uv, tex, camera, W, H):
     zn = ((Lc * inv[tri][:, None, None, :]).sum(-1) - 1.0 / Z_FAR) / (1.0 / Z_NEAR - 1.0 / Z_FAR)
     uvp = (Lc[..., None] * uv[tri][:, None, None, :, :]).sum(-2)  # [m, H, W, 2]
     C = sample_texture(tex, uvp)                                  # [m, H, W, 3]
-    top = torch.maximum(zn.max(dim=0).values, torch.full_like(zn[0], EPS))
-    w = D * torch.exp((zn - top) / GAMMA)
-    wb = torch.exp((EPS - top) / GAMMA)
+    # w_j = D_j exp(zn_j / GAMMA) and the background's exp(EPS / GAMMA), every exponent taken
+    # relative to the largest one present (log D_j = log sigmoid(s_j)): where every D_j has
+    # underflowed the background term stays 1 instead of 0 / 0
+    logw = zn / GAMMA + torch.nn.functional.logsigmoid(Sarg)
+    top = torch.maximum(logw.max(dim=0).values, torch.full_like(zn[0], EPS / GAMMA))
+    w = torch.exp(logw - top)
+    wb = torch.exp(EPS / GAMMA - top)
     img = (w[..., None] * C).sum(0) / (w.sum(0) + wb)[..., None]  # black background
     return img, silhouette(D)
 

@@ -13,7 +13,7 @@
 //                 coordinates of p; blended with weights D_j exp(zn_j / GAMMA) against a
 //                 black background of weight exp(EPS / GAMMA), zn_j the normalised inverse
 //                 depth (1 at Z_NEAR, 0 at Z_FAR) interpolated the same way, evaluated
-//                 relative to the largest exponent;
+//                 relative to the largest exponent (zn_j / GAMMA + log D_j, EPS / GAMMA);
 //   energies      E_p = sum |I - I_hat|_1,  E_s = sum |G(A) - G(B_hat)|_1, G the Gaussian
 //                 of SIGMA_S px truncated at 3 SIGMA_S with zero padding; E = E_p + LAMBDA E_s.
 // The backward pass differentiates these definitions with respect to the vertex positions
@@ -122,10 +122,14 @@ RS_HD void sample(const double* tex, int Wt, int Ht, double u, double v, double*
 }
 
 RS_HD double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+// log sigmoid(z), without overflow or cancellation on either side
+RS_HD double log_sigmoid(double z) { return z >= 0.0 ? -log1p(exp(-z)) : z - log1p(exp(z)); }
 
 // Everything one triangle contributes at one pixel.
 struct TriPix {
   double D, zn, C[3];
+  double s;        // signed sigmoid argument +-d^2 / SIGMA_R (D = sigmoid(s))
+  double logw;     // zn / GAMMA + log D: the log of the triangle's colour weight
   double lam[3];   // barycentric coordinates (unclamped)
   double lc[3];    // clamped, renormalised
   double msum;     // sum of the clamped coordinates
@@ -148,7 +152,8 @@ RS_HD void tri_pixel(P2 p, const P2* q, const double* inv, const double* uv, con
   o->edge = 0;
   if (d1 < d) d = d1, o->edge = 1;
   if (d2 < d) d = d2, o->edge = 2;
-  o->D = sigmoid((o->inside ? d : -d) / SIGMA_R);
+  o->s = (o->inside ? d : -d) / SIGMA_R;
+  o->D = sigmoid(o->s);
   double m[3], s = 0.0;
   for (int k = 0; k < 3; ++k) {
     m[k] = o->lam[k] > 0.0 ? o->lam[k] : 0.0;
@@ -163,16 +168,18 @@ RS_HD void tri_pixel(P2 p, const P2* q, const double* inv, const double* uv, con
     v += o->lc[k] * uv[2 * k + 1];
   }
   o->zn = (zsum - 1.0 / Z_FAR) * zn_scale();
+  o->logw = o->zn / GAMMA + log_sigmoid(o->s);
   sample(tex, Wt, Ht, u, v, o->C, nullptr, nullptr);
 }
 
-// Backward of one triangle at one pixel: given dE/dD, dE/dzn and dE/dC, accumulate
-// dE/d(corner image points) gq[3] and dE/d(corner inverse depths) ginv[3].
+// Backward of one triangle at one pixel: given dE/ds (s the signed sigmoid argument),
+// dE/dzn and dE/dC, accumulate dE/d(corner image points) gq[3] and dE/d(corner inverse
+// depths) ginv[3].
 RS_HD void tri_pixel_backward(P2 p, const P2* q, const double* inv, const double* uv, const double* tex, int Wt,
-                              int Ht, const TriPix& t, double gD, double gzn, const double* gC, P2* gq,
+                              int Ht, const TriPix& t, double gs, double gzn, const double* gC, P2* gq,
                               double* ginv) {
-  // coverage: D = sigmoid(s d^2 / SIGMA_R)
-  const double gd2 = gD * t.D * (1.0 - t.D) * (t.inside ? 1.0 : -1.0) / SIGMA_R;
+  // s = +-d^2 / SIGMA_R
+  const double gd2 = gs * (t.inside ? 1.0 : -1.0) / SIGMA_R;
   const int e0 = t.edge, e1 = (t.edge + 1) % 3;
   seg_d2_grad(p, q[e0], q[e1], gd2, &gq[e0], &gq[e1]);
   // zn and the texture coordinates through the clamped barycentric coordinates
@@ -243,24 +250,27 @@ RS_HD void corners(const Scene& s, int j, P2* q, double* inv, double* uv) {
 }
 
 // Colour I[3] and silhouette A of the pixel centre p.
+// The colour weights w_j = D_j exp(zn_j / GAMMA) and the background's exp(EPS / GAMMA) are
+// evaluated relative to the largest of their exponents (zn_j / GAMMA + log D_j and
+// EPS / GAMMA), so a pixel where every D_j underflows keeps the background's weight 1.
 RS_HD void pixel_forward(const Scene& s, P2 p, double* I, double* A) {
-  double top = EPS;
+  double top = EPS / GAMMA;
   for (int j = 0; j < s.m; ++j) {
     P2 q[3];
     double inv[3], uv[6];
     corners(s, j, q, inv, uv);
     TriPix t;
     tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    top = t.zn > top ? t.zn : top;
+    top = t.logw > top ? t.logw : top;
   }
-  double S = exp((EPS - top) / GAMMA), acc[3] = {0.0, 0.0, 0.0}, prod = 1.0;
+  double S = exp(EPS / GAMMA - top), acc[3] = {0.0, 0.0, 0.0}, prod = 1.0;
   for (int j = 0; j < s.m; ++j) {
     P2 q[3];
     double inv[3], uv[6];
     corners(s, j, q, inv, uv);
     TriPix t;
     tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    const double w = t.D * exp((t.zn - top) / GAMMA);
+    const double w = exp(t.logw - top);
     S += w;
     for (int k = 0; k < 3; ++k) acc[k] += w * t.C[k];
     prod *= 1.0 - t.D;
@@ -273,17 +283,17 @@ RS_HD void pixel_forward(const Scene& s, P2 p, double* I, double* A) {
 // gradient with respect to vertex v's image point and inverse depth.
 template <class Add>
 RS_HD void pixel_backward(const Scene& s, P2 p, const double* gI, double gA, Add add) {
-  double top = EPS;
+  double top = EPS / GAMMA;
   for (int j = 0; j < s.m; ++j) {
     P2 q[3];
     double inv[3], uv[6];
     corners(s, j, q, inv, uv);
     TriPix t;
     tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    top = t.zn > top ? t.zn : top;
+    top = t.logw > top ? t.logw : top;
   }
   // first pass: S, I, the product of the non-zero (1 - D) factors and the zero count
-  double S = exp((EPS - top) / GAMMA), acc[3] = {0.0, 0.0, 0.0}, pnz = 1.0;
+  double S = exp(EPS / GAMMA - top), acc[3] = {0.0, 0.0, 0.0}, pnz = 1.0;
   int zeros = 0;
   for (int j = 0; j < s.m; ++j) {
     P2 q[3];
@@ -291,7 +301,7 @@ RS_HD void pixel_backward(const Scene& s, P2 p, const double* gI, double gA, Add
     corners(s, j, q, inv, uv);
     TriPix t;
     tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    const double w = t.D * exp((t.zn - top) / GAMMA);
+    const double w = exp(t.logw - top);
     S += w;
     for (int k = 0; k < 3; ++k) acc[k] += w * t.C[k];
     if (1.0 - t.D == 0.0) ++zeros;
@@ -305,19 +315,20 @@ RS_HD void pixel_backward(const Scene& s, P2 p, const double* gI, double gA, Add
     corners(s, j, q, inv, uv);
     TriPix t;
     tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    // a triangle whose coverage underflowed to 0 contributes exactly nothing here (its
-    // weight, the coverage derivative D (1 - D) and its colour share are all 0)
-    if (t.D == 0.0) continue;
-    const double e = exp((t.zn - top) / GAMMA), w = t.D * e;
+    const double w = exp(t.logw - top);
+    // a triangle whose weight and coverage both underflowed to 0 contributes exactly nothing
+    // here (dE/ds, dE/dzn and its colour share are all 0)
+    if (w == 0.0 && t.D == 0.0) continue;
     const double gw = (gI[0] * (t.C[0] - I[0]) + gI[1] * (t.C[1] - I[1]) + gI[2] * (t.C[2] - I[2])) / S;
     const double gC[3] = {gI[0] * w / S, gI[1] * w / S, gI[2] * w / S};
     const double om = 1.0 - t.D;
     const double others = om == 0.0 ? (zeros == 1 ? pnz : 0.0) : (zeros == 0 ? pnz / om : 0.0);
-    const double gD = gw * e + gA * others;
+    // dw/ds = w (1 - D) (d log sigmoid(s) / ds = 1 - D), dA/ds = others D (1 - D), dw/dzn = w / GAMMA
+    const double gs = (gw * w + gA * others * t.D) * om;
     const double gzn = gw * w / GAMMA;
     P2 gq[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
     double ginv[3] = {0.0, 0.0, 0.0};
-    tri_pixel_backward(p, q, inv, uv, s.tex, s.Wt, s.Ht, t, gD, gzn, gC, gq, ginv);
+    tri_pixel_backward(p, q, inv, uv, s.tex, s.Wt, s.Ht, t, gs, gzn, gC, gq, ginv);
     for (int k = 0; k < 3; ++k) add(s.tris[3 * j + k], gq[k].x, gq[k].y, ginv[k]);
   }
 }

@@ -10,14 +10,14 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("seed", [1, 2])
-def test_image_energy_matches_oracle(seed):
+@pytest.mark.parametrize("seed,W,H", [(1, 24, 20), (2, 24, 20), (3, 96, 80)])
+def test_image_energy_matches_oracle(seed, W, H):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from oracle import softras as S
     from paper_2203_11938_gb300 import sim
 
-    x, tris, tri, uv, tex, cam, image, mask = scene(seed)
+    x, tris, tri, uv, tex, cam, image, mask = scene(seed, W, H)
     cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
     E, g, img, sil = sim.image_energy(cu(x), tris, cu(uv), cu(tex), cam, cu(image), cu(mask), want_grad=True,
                                       want_render=True)

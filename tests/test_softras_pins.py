@@ -16,8 +16,8 @@ def test_edge_and_corner_probabilities():
     with d the distance to the nearest edge line, outside pixels below an edge
     sigmoid(-d^2/sigma) (right triangle with legs on pixel-centre lines)."""
     q = torch.tensor([[2.5, 2.5], [14.5, 2.5], [2.5, 14.5]], dtype=torch.float64)
-    D, _ = S.coverage(q, [(0, 1, 2)], 16, 16)
-    D = D[0].numpy()
+    s_, _ = S.coverage(q, [(0, 1, 2)], 16, 16)
+    D = torch.sigmoid(s_)[0].numpy()
     assert D[2, 6] == pytest.approx(0.5, abs=1e-15)  # centre (6.5, 2.5) on the edge y = 2.5
     for (v, u) in [(5, 5), (4, 7), (6, 4), (8, 3)]:
         x, y = u + 0.5, v + 0.5
@@ -34,8 +34,8 @@ def test_soft_union_on_a_shared_edge():
     bottom and right edges and 6/sqrt(2) px from the diagonal, it is
     1 - (1 - sigmoid(4)) (1 - sigmoid(-18))."""
     q = torch.tensor([[2.5, 2.5], [12.5, 2.5], [12.5, 12.5], [2.5, 12.5]], dtype=torch.float64)
-    D, _ = S.coverage(q, [(0, 1, 2), (0, 2, 3)], 16, 16)
-    A = S.silhouette(D).numpy()
+    s_, _ = S.coverage(q, [(0, 1, 2), (0, 2, 3)], 16, 16)
+    A = S.silhouette(torch.sigmoid(s_)).numpy()
     assert A[7, 7] == pytest.approx(0.75, abs=1e-12)  # centre (7.5, 7.5) on the diagonal
     assert A[4, 10] == pytest.approx(1 - (1 - sig(4.0)) * (1 - sig(-18.0)), rel=1e-12)
 
@@ -57,12 +57,61 @@ def test_colour_blend_closed_form_constant_texture():
     tex = np.broadcast_to(c, (4, 4, 3)).copy()
     img, A = S.render(x, tris, uv, tex, cam, 32, 32)
     q, depth = S.project(torch.as_tensor(x), cam, 32, 32)
-    D, _ = S.coverage(q, tris, 32, 32)
-    D = D[0].numpy()
+    s_, _ = S.coverage(q, tris, 32, 32)
+    D = torch.sigmoid(s_)[0].numpy()
     zn = (1 / 2.0 - 1 / S.Z_FAR) / (1 / S.Z_NEAR - 1 / S.Z_FAR)
     wb = math.exp((S.EPS - zn) / S.GAMMA)
     expect = c[None, None, :] * (D / (D + wb))[..., None]
     np.testing.assert_allclose(img.numpy(), expect, rtol=1e-12, atol=1e-300)
+
+
+def _logsig(z):
+    """log sigmoid(z), written out for the closed forms below."""
+    return -math.log1p(math.exp(-z)) if z >= 0 else z - math.log1p(math.exp(z))
+
+
+def _one_triangle_at_pixels(corners_px, depth, cam, W, H):
+    """World corners at `depth` in front of the camera whose images are the given pixel
+    coordinates (the inverse of the pinhole with the principal point at the centre)."""
+    f, cx, cy, cz = cam
+    return np.array([[cx + (u - W / 2) * depth / f, cy - (v - H / 2) * depth / f, cz - depth] for u, v in corners_px])
+
+
+def test_colour_blend_away_from_the_sheet_closed_form():
+    """Outside a triangle the colour is c D e^{zn/GAMMA} / (D e^{zn/GAMMA} + e^{EPS/GAMMA})
+    = c sigmoid(zn/GAMMA + log D - EPS/GAMMA), D = sigmoid(-d^2/SIGMA_R): at depth 4 m
+    (zn = 1/36) a pixel centre 16.5 px above the triangle's top edge shows about 1 % of
+    the texture colour, a value that dropping the coverage term, the depth term or the
+    background would each change."""
+    W = H = 128
+    cam = (100.0, 0.5, 0.5, 4.0)
+    x = _one_triangle_at_pixels([(40.0, 64.0), (90.0, 64.0), (64.0, 110.0)], 4.0, cam, W, H)
+    c = np.array([0.2, 0.5, 0.9])
+    tex = np.broadcast_to(c, (4, 4, 3)).copy()
+    uv = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0]])
+    img, _ = S.render(x, [(0, 1, 2)], uv, tex, cam, W, H)
+    zn = (1 / 4.0 - 1 / S.Z_FAR) / (1 / S.Z_NEAR - 1 / S.Z_FAR)
+    d = 64.0 - 47.5  # pixel (64, 47): centre (64.5, 47.5), nearest point (64.5, 64) on the top edge
+    share = 1.0 / (1.0 + math.exp(-(zn / S.GAMMA + _logsig(-d * d / S.SIGMA_R) - S.EPS / S.GAMMA)))
+    assert 1e-3 < share < 0.1
+    np.testing.assert_allclose(img[47, 64].numpy(), c * share, rtol=1e-9)
+
+
+def test_background_far_from_every_triangle_is_black_not_nan():
+    """Where every coverage underflows (a pixel tens of pixels from the sheet, here at
+    2 m, zn = 1/6) the blend is the black background: 0, finite, with a finite gradient."""
+    W = H = 96
+    cam = (100.0, 0.5, 0.5, 2.0)
+    x = torch.tensor(_one_triangle_at_pixels([(60.0, 60.0), (90.0, 60.0), (75.0, 90.0)], 2.0, cam, W, H),
+                     requires_grad=True)
+    tex = np.full((4, 4, 3), 0.7)
+    uv = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0]])
+    img, A = S.render(x, [(0, 1, 2)], uv, tex, cam, W, H)
+    assert torch.isfinite(img).all() and torch.isfinite(A).all()
+    assert float(img[0, 0].abs().max()) == 0.0 and float(A[0, 0]) == 0.0  # ~80 px from the triangle
+    assert float(img[75, 75].min()) > 0.69  # inside: the texture colour
+    (g,) = torch.autograd.grad(img.sum(), x)
+    assert torch.isfinite(g).all()
 
 
 def test_nearer_triangle_wins():
