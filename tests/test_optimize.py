@@ -167,7 +167,9 @@ def test_fit_with_image_frame_loss_masks_and_assembles_frames():
     for t in range(1, T + 1):
         if t <= 5:
             _, g = energy_fn(traj0[t], t)
-            np.testing.assert_allclose(dL[t].numpy(), g.numpy(), rtol=1e-12, atol=0)
+            # fit() simulates exp(log p), one rounding away from p: entries that are zero up
+            # to rounding (~1e-13 against a largest entry of order 1) differ at that level
+            np.testing.assert_allclose(dL[t].numpy(), g.numpy(), rtol=1e-12, atol=1e-11 * float(g.abs().max()))
         else:
             assert torch.all(dL[t] == 0)
     assert torch.any(dL[1:6] != 0)
