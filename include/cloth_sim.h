@@ -95,7 +95,8 @@ typedef struct cloth_opts {
                                -1 = autotune at cloth_batch_create (times each schedule
                                on the batch's matrix, caches the choice in the JSON file
                                $CLOTH_TUNE_CACHE or ~/.cache/cloth_sim/tune.json);
-                               0..31: bit 1 = direction update folded into the SpMV,
+                               0..31: bit 1 is always set (the direction update is
+                               folded into the SpMV; a value without it means the same),
                                bit 0 = resident-CTA grid looping over rows, bit 2 =
                                per-sheet cluster solver for the sheets still iterating
                                at the hand-over point (every sheet of at most 8192

@@ -75,8 +75,8 @@ struct Dev {
   double *tri_f, *hin_f;  // element force vectors f_e - h H~_e v_e, FP64
   R *tri_H, *hin_H, *tri_r, *hin_r;
   double *tri_sc, *hin_sc, *row_sc;
-  R *Aval, *bvec, *r, *z, *Ap;
-  R* p;  // two direction buffers [2][Np][3] (p_k and p_{k-1})
+  R *Aval, *bvec, *r, *Ap;
+  R* zp;  // CG gather records [2][Np][8]: buffer k & 1 holds (z_k, p_{k-1}) of iteration k
   R* pg;  // a solve's starting guess in the direction layout (warm start), or null
   R* dinv;  // [9][Np] inverse of each vertex's 3x3 diagonal block (block Jacobi) or its diagonal
   double* dv;  // CG solution (dv, or lambda in the adjoint): FP64 after each solve
@@ -149,6 +149,48 @@ template <class R> __device__ __forceinline__ void stp(R* a, int i, V3<R> v) { s
 template <> __device__ __forceinline__ void stp<float>(float* a, int i, V3<float> v) {
   reinterpret_cast<float4*>(a)[i] = make_float4(v.x, v.y, v.z, 0.f);
 }
+// CG gather records.  In iteration k every row's SpMV reads, for itself and each
+// neighbour j, z_k[j] and the previous direction p_{k-1}[j]; both live in one record of
+// 8 reals (x, y, z, 0 of z_k, then of p_{k-1}), so a neighbour costs one aligned 32-byte
+// load in FP32 (two 32-byte loads in FP64).  Buffer k & 1 holds the records of iteration
+// k; iteration k writes p_k and z_{k+1} into buffer (k + 1) & 1.
+template <class R> struct Rec {
+  V3<R> z, p;
+};
+template <class R> __device__ __forceinline__ R* rec(const Dev<R>& d, int k, int i) {
+  return d.zp + ((size_t)(k & 1) * d.Np + i) * 8;
+}
+// a record through L1 (values written by earlier kernels) or L2 only (values written by
+// other SMs during the same kernel, after a cluster barrier)
+template <class R> __device__ __forceinline__ Rec<R> ld_rec(const R* a) {
+  return {ld3(a, 0), {a[4], a[5], a[6]}};
+}
+template <class R> __device__ __forceinline__ Rec<R> ld_rec_l2(const R* a) {
+  return {{__ldcg(a), __ldcg(a + 1), __ldcg(a + 2)}, {__ldcg(a + 4), __ldcg(a + 5), __ldcg(a + 6)}};
+}
+template <> __device__ __forceinline__ Rec<float> ld_rec<float>(const float* a) {
+  float v[8];
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(a));
+  return {{v[0], v[1], v[2]}, {v[4], v[5], v[6]}};
+}
+template <> __device__ __forceinline__ Rec<float> ld_rec_l2<float>(const float* a) {
+  float v[8];
+  asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(a));
+  return {{v[0], v[1], v[2]}, {v[4], v[5], v[6]}};
+}
+template <class R> __device__ __forceinline__ void st_rec_z(R* a, V3<R> z) { st3(a, 0, z); }
+template <class R> __device__ __forceinline__ void st_rec_p(R* a, V3<R> p) { st3(a + 4, 0, p); }
+template <> __device__ __forceinline__ void st_rec_z<float>(float* a, V3<float> z) {
+  *reinterpret_cast<float4*>(a) = make_float4(z.x, z.y, z.z, 0.f);
+}
+template <> __device__ __forceinline__ void st_rec_p<float>(float* a, V3<float> p) {
+  *reinterpret_cast<float4*>(a + 4) = make_float4(p.x, p.y, p.z, 0.f);
+}
+
 // streamed (read-once) matrix data: do not keep in L1
 template <class R> __device__ __forceinline__ R lds(const R* a) { return __ldcs(a); }
 template <class R> __device__ __forceinline__ V3<R> axpy3(R s, V3<R> x, V3<R> y) {
@@ -784,13 +826,12 @@ __global__ void k_cond_set(Dev<R> d, cudaGraphConditionalHandle cond) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, *d.active > d.tail_threshold ? 1u : 0u);
 }
 
-// Jacobi-PCG over all sheets at once.  The streaming kernels (init, SpMV, update,
-// direction) write one FP64 partial sum per warp and use no barrier, fence or atomic;
-// a per-sheet scalar kernel (one warp per sheet, fixed summation order, hence
-// deterministic) then forms alpha, or beta and the convergence test.  Iteration k of a
-// sheet uses p_k = z_k + beta_k p_{k-1} (beta_0 = 0), kept in pbuf[k & 1]; the SpMV either
-// forms p_k itself (FUSED: own row written, neighbours on the fly, same fused multiply-add,
-// so bitwise the values k_cg_dir would write) or reads what k_cg_dir wrote.
+// Jacobi-PCG over all sheets at once.  The streaming kernels (init, SpMV, update) write one
+// partial sum per warp and use no barrier, fence or atomic; a per-sheet scalar kernel (one
+// warp per sheet, fixed summation order, hence deterministic) then forms alpha, or beta and
+// the convergence test.  Iteration k of a sheet uses p_k = z_k + beta_k p_{k-1}
+// (beta_0 = 0), which the SpMV forms from the gather records for the own row and every
+// neighbour (the same fused multiply-add everywhere, so every copy is bitwise the same).
 template <class R>
 __device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
   return {fma_rn(beta, pold.x, z.x), fma_rn(beta, pold.y, z.y), fma_rn(beta, pold.z, z.z)};
@@ -799,7 +840,7 @@ __device__ __forceinline__ V3<R> next_dir(V3<R> z, R beta, V3<R> pold) {
 // partial of warp `wp` (0..7) of work entry w: index w * 8 + wp
 constexpr int kWarpsPerEntry = kThreads / 32;
 
-// r = rhs, dv = 0, z = D^{-1} r, p_0 = z, p_{-1} = 0; partials of r.z and r.r.
+// r = rhs, dv = 0, z_0 = D^{-1} r, p_{-1} = 0 (record buffer 0); partials of r.z and r.r.
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restrict__ rhs) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -811,9 +852,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Dev<R> d, const R* __restr
       const V3<R> r = ld3(rhs, i);
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
       st3(d.r, i, r);
-      st3(d.z, i, z);
-      stp(d.p, i, z);                                                          // p_0 (buffer 0)
-      stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
+      st_rec_z(rec(d, 0, i), z);                      // z_0
+      st_rec_p(rec(d, 0, i), V3<R>{R(0), R(0), R(0)});  // p_{-1} = 0
       if constexpr (std::is_same<R, float>::value) {
         st3(d.dvh, i, V3<float>{0.f, 0.f, 0.f});
         st3(d.dvl, i, V3<float>{0.f, 0.f, 0.f});
@@ -854,26 +894,20 @@ __global__ void k_cg_scalar_init(Dev<R> d, int phase, int guess) {
   if (cg_init_step<R>(d.cg[s], rz, rr, bb, d.tol)) finish_sheet(d, s, phase, 0, 0);
 }
 
-// One row of the SpMV: Ap_i = (A p_k)_i in difference form; returns p_i . Ap_i (or 0).
-template <class R, bool FUSED>
-__device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, const R* __restrict__ pold,
-                                           R* __restrict__ pnew) {
+// One row of A v in difference form, (A v)_i = R_i v_i + sum_{j != i} A_ij (v_j - v_i), for
+// the row's own value vi and gather(j) giving v_j (two slots per loop iteration: more loads
+// in flight).
+template <class R, class G>
+__device__ __forceinline__ V3<R> spmv_core(const Dev<R>& d, int i, V3<R> vi, G gather) {
   const int sl = i >> 5, lane = i & 31;
   const int K = d.slice_K[sl], base = d.slice_base[sl];
-  V3<R> pi;
-  if (FUSED) {
-    pi = next_dir(ld3(d.z, i), beta, ldp(pold, i));
-    stp(pnew, i, pi);
-  } else {
-    pi = ldp(pnew, i);
-  }
   const R* a0 = d.Aval + (size_t)base * 32 * 9 + lane;
   R ab[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) ab[t] = lds(a0 + 32 * t);
-  V3<R> y = block_mul(ab, pi);
+  V3<R> y = block_mul(ab, vi);
   int q = 1;
-  for (; q + 1 < K; q += 2) {  // two slots per iteration: more loads in flight
+  for (; q + 1 < K; q += 2) {
     const int e0 = (base + q) * 32 + lane, e1 = e0 + 32;
     const int j0 = lds(d.cols + e0), j1 = lds(d.cols + e1);
     const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + lane;
@@ -884,10 +918,9 @@ __device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, con
       av[t] = lds(a + 32 * t);
       bv[t] = lds(b + 32 * t);
     }
-    const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
-    const V3<R> p1 = FUSED ? next_dir(ld3(d.z, j1), beta, ldp(pold, j1)) : ldp(pnew, j1);
-    block_acc(y, av, V3<R>{p0.x - pi.x, p0.y - pi.y, p0.z - pi.z});
-    block_acc(y, bv, V3<R>{p1.x - pi.x, p1.y - pi.y, p1.z - pi.z});
+    const V3<R> p0 = gather(j0), p1 = gather(j1);
+    block_acc(y, av, V3<R>{p0.x - vi.x, p0.y - vi.y, p0.z - vi.z});
+    block_acc(y, bv, V3<R>{p1.x - vi.x, p1.y - vi.y, p1.z - vi.z});
   }
   if (q < K) {
     const int e0 = (base + q) * 32 + lane;
@@ -896,9 +929,24 @@ __device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, con
     R av[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) av[t] = lds(a + 32 * t);
-    const V3<R> p0 = FUSED ? next_dir(ld3(d.z, j0), beta, ldp(pold, j0)) : ldp(pnew, j0);
-    block_acc(y, av, V3<R>{p0.x - pi.x, p0.y - pi.y, p0.z - pi.z});
+    const V3<R> p0 = gather(j0);
+    block_acc(y, av, V3<R>{p0.x - vi.x, p0.y - vi.y, p0.z - vi.z});
   }
+  return y;
+}
+
+// One row of the CG SpMV of iteration k: p_k = z_k + beta_k p_{k-1} formed from the records
+// for the row (and stored as the row's p_k) and for every neighbour, Ap_i = (A p_k)_i;
+// returns p_i . Ap_i.
+template <class R>
+__device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, int k) {
+  const Rec<R> own = ld_rec(rec(d, k, i));
+  const V3<R> pi = next_dir(own.z, beta, own.p);
+  st_rec_p(rec(d, k + 1, i), pi);
+  const V3<R> y = spmv_core(d, i, pi, [&](int j) {
+    const Rec<R> n = ld_rec(rec(d, k, j));
+    return next_dir(n.z, beta, n.p);
+  });
   st3(d.Ap, i, y);
   return acc_dot3(pi, y);
 }
@@ -906,10 +954,11 @@ __device__ __forceinline__ acc_t<R> spmv_row(const Dev<R>& d, int i, R beta, con
 // One row of the update: dv += alpha p_k (FP64, or float-float in FP32 mode),
 // r -= alpha Ap, z = D^{-1} r (stored).
 template <class R>
-__device__ __forceinline__ void update_row(const Dev<R>& d, int i, acc_t<R> al, const R* __restrict__ pk,
-                                           acc_t<R>& rz, acc_t<R>& rr) {
+__device__ __forceinline__ void update_row(const Dev<R>& d, int i, acc_t<R> al, int k, acc_t<R>& rz,
+                                           acc_t<R>& rr) {
   const R alpha = alpha_cast(al);
-  const V3<R> p = ldp(pk, i), Ap = ld3(d.Ap, i);
+  R* rk1 = rec(d, k + 1, i);  // holds p_k (written by this iteration's SpMV); receives z_{k+1}
+  const V3<R> p = ld_rec(rk1).p, Ap = ld3(d.Ap, i);
   V3<R> r = ld3(d.r, i);
   if constexpr (std::is_same<R, float>::value) {
     const V3<float> xh = ld3(d.dvh, i), xl = ld3(d.dvl, i);
@@ -926,7 +975,7 @@ __device__ __forceinline__ void update_row(const Dev<R>& d, int i, acc_t<R> al, 
   r = {fma_rn(-alpha, Ap.x, r.x), fma_rn(-alpha, Ap.y, r.y), fma_rn(-alpha, Ap.z, r.z)};
   st3(d.r, i, r);
   const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
-  st3(d.z, i, z);
+  st_rec_z(rk1, z);
   rz = acc_dot3(r, z);
   rr = acc_dot3(r, r);
 }
@@ -949,7 +998,7 @@ __global__ void k_cg_guess(Dev<R> d, const double* __restrict__ guess) {
 }
 
 // Solve started from the guess of k_cg_guess: r = rhs - A g (the SpMV's difference form),
-// z = D^{-1} r, p_0 = z, p_{-1} = 0; partials of r.z, r.r and |rhs|^2 (the stopping test
+// z_0 = D^{-1} r, p_{-1} = 0; partials of r.z, r.r and |rhs|^2 (the stopping test
 // stays |r| <= tol |b|).
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_init_guess(Dev<R> d, const R* __restrict__ rhs) {
@@ -959,14 +1008,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_init_guess(Dev<R> d, const R* _
     const int i = d.work_row0[w] + threadIdx.x;
     acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>(), v2 = acc_zero<R>();
     if (on) {
-      spmv_row<R, false>(d, i, R(0), nullptr, d.pg);  // A g into d.Ap
-      const V3<R> b = ld3(rhs, i), ag = ld3(d.Ap, i);
+      const V3<R> ag = spmv_core(d, i, ldp(d.pg, i), [&](int j) { return ldp(d.pg, j); });  // A g
+      const V3<R> b = ld3(rhs, i);
       const V3<R> r = {add_rn(b.x, -ag.x), add_rn(b.y, -ag.y), add_rn(b.z, -ag.z)};
       const V3<R> z = apply_dinv(d.dinv, d.Np, i, r);
       st3(d.r, i, r);
-      st3(d.z, i, z);
-      stp(d.p, i, z);                                                          // p_0 (buffer 0)
-      stp(d.p + PStride<R>::v * (size_t)d.Np, i, V3<R>{R(0), R(0), R(0)});  // p_{-1} (buffer 1)
+      st_rec_z(rec(d, 0, i), z);                      // z_0
+      st_rec_p(rec(d, 0, i), V3<R>{R(0), R(0), R(0)});  // p_{-1} = 0
       v0 = acc_dot3(r, z);
       v1 = acc_dot3(r, r);
       v2 = acc_dot3(b, b);
@@ -999,13 +1047,8 @@ __global__ void k_cg_solution(Dev<R> d, double* __restrict__ keep) {
   if (keep) st3(keep, i, x);
 }
 
-template <class R>
-__device__ __forceinline__ const R* pbuf(const Dev<R>& d, int parity) {
-  return d.p + PStride<R>::v * (size_t)d.Np * (parity & 1);
-}
-
 // Ap = A p_k over all active sheets; warp partials of p.Ap.
-template <class R, bool FUSED>
+template <class R>
 __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
   const int lane_w = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
@@ -1015,7 +1058,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_spmv(Dev<R> d) {
     const R beta = beta_of<R>(d.cg[s]);
     acc_t<R> v = acc_zero<R>();
     if (threadIdx.x < d.work_rows[w])
-      v = spmv_row<R, FUSED>(d, d.work_row0[w] + threadIdx.x, beta, pbuf(d, k + 1), const_cast<R*>(pbuf(d, k)));
+      v = spmv_row<R>(d, d.work_row0[w] + threadIdx.x, beta, k);
     const acc_t<R> t = acc_warp_total(v);
     if (lane_w == 0) d.part_c[(size_t)w * kWarpsPerEntry + wp] = t;
   }
@@ -1041,7 +1084,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Dev<R> d) {
     const int k = d.cg[s].iters;
     acc_t<R> v0 = acc_zero<R>(), v1 = acc_zero<R>();
     if (threadIdx.x < d.work_rows[w])
-      update_row(d, d.work_row0[w] + threadIdx.x, alpha_of<R>(d.cg[s]), pbuf(d, k), v0, v1);
+      update_row(d, d.work_row0[w] + threadIdx.x, alpha_of<R>(d.cg[s]), k, v0, v1);
     const acc_t<R> t0 = acc_warp_total(v0), t1 = acc_warp_total(v1);
     if (lane_w == 0) {
       d.part_a[(size_t)w * kWarpsPerEntry + wp] = t0;
@@ -1060,22 +1103,6 @@ __global__ void k_cg_scalar_beta(Dev<R> d, int phase, cudaGraphConditionalHandle
   const acc_t<R> rz = sheet_sum(d, d.part_a, s), rr = sheet_sum(d, d.part_b, s);
   if ((threadIdx.x & 31) != 0) return;
   if (cg_beta_step<R>(d.cg[s], rz, rr, d.maxit)) finish_sheet(d, s, phase, cond, use_cond);
-}
-
-// p_{k+1} = z_{k+1} + beta_{k+1} p_k (separate-direction schedule), after k_cg_scalar_beta
-template <class R>
-__global__ void __launch_bounds__(kThreads) k_cg_dir(Dev<R> d) {
-  for (int w = blockIdx.x; w < d.NW; w += gridDim.x) {
-    const int s = d.work_sheet[w];
-    if (d.cg[s].done) continue;
-    if (threadIdx.x >= d.work_rows[w]) continue;
-    const int k = d.cg[s].iters;  // already k + 1
-    const R beta = beta_of<R>(d.cg[s]);
-    const R* __restrict__ pold = d.p + PStride<R>::v * (size_t)d.Np * ((k + 1) & 1);
-    R* __restrict__ pnew = d.p + PStride<R>::v * (size_t)d.Np * (k & 1);
-    const int i = d.work_row0[w] + threadIdx.x;
-    stp(pnew, i, next_dir(ld3(d.z, i), beta, ldp(pold, i)));
-  }
 }
 
 // ------------------------------------------------------------------ per-sheet cluster solver
@@ -1122,16 +1149,8 @@ template <> struct DvReg<float> {
 };
 
 // The matrix, its column indices and the block-Jacobi inverse do not change during a
-// solve and are read through the read-only (L1) path; values written by other threads
-// in the previous phase (z, p) are read through L2.
-template <class R> __device__ __forceinline__ V3<R> ld3_l2(const R* a, int i) {
-  return {__ldcg(a + 3 * (size_t)i), __ldcg(a + 3 * (size_t)i + 1), __ldcg(a + 3 * (size_t)i + 2)};
-}
-template <class R> __device__ __forceinline__ V3<R> ldp_l2(const R* a, int i) { return ld3_l2(a, i); }
-template <> __device__ __forceinline__ V3<float> ldp_l2<float>(const float* a, int i) {
-  const float4 q = __ldcg(reinterpret_cast<const float4*>(a) + i);
-  return {q.x, q.y, q.z};
-}
+// solve and are read through the read-only (L1) path; the gather records written by other
+// CTAs in the previous phase are read through L2 (ld_rec_l2).
 
 // MINB: CTAs per SM the register budget is sized for (3 for the dense one-entry classes,
 // which put several sheets' CTAs on each SM so that one sheet's barrier waits overlap
@@ -1210,8 +1229,9 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   const int sl_lane = i & 31;
   if (on) {
     r = ld3(d.r, i);
-    z = ld3(d.z, i);
-    pold = ldp(pbuf(d, k + 1), i);
+    const Rec<R> own = ld_rec_l2(rec(d, k, i));
+    z = own.z;
+    pold = own.p;
     x.load(d, i);
     const int sl = i >> 5;
     K = d.slice_K[sl];
@@ -1229,9 +1249,8 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
     acc_t<R> vpart = acc_zero<R>();
     V3<R> pi = {R(0), R(0), R(0)};
     if (on) {
-      const R* __restrict__ pprev = pbuf(d, k + 1);
       pi = next_dir(z, beta_r, pold);
-      stp(const_cast<R*>(pbuf(d, k)), i, pi);
+      st_rec_p(rec(d, k + 1, i), pi);  // read by the neighbours as p_k in the next iteration
       const R* a0 = d.Aval + (size_t)base * 32 * 9 + sl_lane;
       R ab[9];
 #pragma unroll
@@ -1245,7 +1264,8 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
           R av[9];
 #pragma unroll
           for (int m = 0; m < 9; ++m) av[m] = __ldg(a + 32 * m);
-          const V3<R> pj = next_dir(ld3_l2(d.z, j), beta_r, ldp_l2(pprev, j));
+          const Rec<R> nj = ld_rec_l2(rec(d, k, j));
+          const V3<R> pj = next_dir(nj.z, beta_r, nj.p);
           block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
         }
       }
@@ -1255,7 +1275,8 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
         R av[9];
 #pragma unroll
         for (int m = 0; m < 9; ++m) av[m] = __ldg(a + 32 * m);
-        const V3<R> pj = next_dir(ld3_l2(d.z, j), beta_r, ldp_l2(pprev, j));
+        const Rec<R> nj = ld_rec_l2(rec(d, k, j));
+        const V3<R> pj = next_dir(nj.z, beta_r, nj.p);
         block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
       }
       Ap = y;
@@ -1289,7 +1310,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
         for (int m = 0; m < 9; ++m) dm[m] = __ldg(d.dinv + (size_t)m * d.Np + i);
         z = block_mul(dm, r);  // = apply_dinv
       }
-      st3(d.z, i, z);  // gathered by the neighbours in the next iteration
+      st_rec_z(rec(d, k + 1, i), z);  // gathered by the neighbours in the next iteration
       va = acc_dot3(r, z);
       vb = acc_dot3(r, r);
       pold = pi;
@@ -1405,8 +1426,9 @@ __global__ void __launch_bounds__(kSmMaxThreads, 1) k_cg_sheet_sm(Dev<R> d, cons
   int K = 0, lb = 0, col[kSmSlots - 1];
   if (on) {
     r = ld3(d.r, i);
-    z = ld3(d.z, i);
-    pold = ldp(pbuf(d, k + 1), i);
+    const Rec<R> own = ld_rec_l2(rec(d, k, i));
+    z = own.z;
+    pold = own.p;
     x.load(d, i);
     const int sl = i >> 5;
     K = d.slice_K[sl];

@@ -154,8 +154,7 @@ class Engine final : public EngineBase {
     d.bvec = alloc<R>(n3, &rc);
     d.dinv = alloc<R>(9 * (size_t)L_.Np, &rc);
     d.r = alloc<R>(n3, &rc);
-    d.p = alloc<R>(2 * (size_t)PStride<R>::v * L_.Np, &rc);
-    d.z = alloc<R>(n3, &rc);
+    d.zp = alloc<R>(2 * 8 * (size_t)L_.Np, &rc);
     d.Ap = alloc<R>(n3, &rc);
     d.dv = alloc<double>(n3, &rc);
     if (o_.cg_warm_start) {
@@ -219,18 +218,16 @@ class Engine final : public EngineBase {
     }
     // CG kernels of the resident-grid schedules: as many CTAs as can be resident at once
     // (each kernel by its own occupancy), each looping over work entries
-    int dev = 0, sms = 0, per_sm = 0, per_sm_f = 0, per_sm2 = 0;
+    int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R, false>, kThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_cg_spmv<R, true>, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_spmv<R>, kThreads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_update<R>, kThreads, 0) != cudaSuccess) {
       *err = "CUDA occupancy query failed";
       return CLOTH_ERR_CUDA;
     }
     auto resident = [&](int per) { return std::max(1, std::min(d.NW, sms * std::max(1, per))); };
-    res_spmv_[0] = resident(per_sm);
-    res_spmv_[1] = resident(per_sm_f);
+    res_spmv_ = resident(per_sm);
     res_upd_ = resident(per_sm2);
     spmv_grid_ = upd_grid_ = d.NW;
     // per-sheet cluster solvers: every sheet of at most 8 x 4 work entries (8192 rows) gets a
@@ -341,7 +338,7 @@ class Engine final : public EngineBase {
     if (fwd) *fwd = (int64_t)h[0];
     if (bwd) *bwd = (int64_t)h[1];
     if (rec) *rec = (int64_t)h[2];
-    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + (sched_fused_ ? 4 : 5) * (int64_t)(b[0] + b[1] + b[2]);
+    if (launches) *launches = fixed_fwd_ + fixed_bwd_ + 4 * (int64_t)(b[0] + b[1] + b[2]);
     return CLOTH_OK;
   }
 
@@ -394,8 +391,7 @@ class Engine final : public EngineBase {
     const int64_t stored = (int64_t)L_.total_slots() * 32;
     switch (which) {
       case 0:  // 3x3 values + column per nonzero block; z, p_{k-1} read and p_k, Ap written
-               // (fused) or p_k read and Ap written
-        *out = nonzero_blocks() * (9 * es + 4) + rows * (sched_fused_ ? 4 : 2) * 3 * es;
+        *out = nonzero_blocks() * (9 * es + 4) + rows * 4 * 3 * es;
         break;
       case 1:  // p, Ap, r read; r, z written; 3x3 inverse; the solution read and written (24 B each)
         *out = rows * (5 * 3 * es + 9 * es + 48);
@@ -433,8 +429,7 @@ class Engine final : public EngineBase {
     auto one = [&]() {
       switch (which) {
         case 0:
-          if (sched_fused_) k_cg_spmv<R, true><<<spmv_grid_, kThreads, 0, st>>>(d_);
-          else k_cg_spmv<R, false><<<spmv_grid_, kThreads, 0, st>>>(d_);
+          k_cg_spmv<R><<<spmv_grid_, kThreads, 0, st>>>(d_);
           break;
         case 1: k_cg_update<R><<<upd_grid_, kThreads, 0, st>>>(d_); break;
         case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr, nullptr); break;
@@ -854,8 +849,8 @@ class Engine final : public EngineBase {
     use_dense_ = (schedule_ & 16) != 0 && !use_sm_ && dense_ok_;
     if (!use_sm_) schedule_ &= ~8;
     if (!use_dense_) schedule_ &= ~16;
-    sched_fused_ = (schedule_ & 2) != 0;
-    spmv_grid_ = (schedule_ & 1) ? res_spmv_[sched_fused_ ? 1 : 0] : d_.NW;
+    schedule_ |= 2;  // the direction update is always folded into the SpMV
+    spmv_grid_ = (schedule_ & 1) ? res_spmv_ : d_.NW;
     upd_grid_ = (schedule_ & 1) ? res_upd_ : d_.NW;
     // bit 2: every sheet is solved by the per-sheet cluster solver (the device loop
     // hands over at once)
@@ -865,12 +860,10 @@ class Engine final : public EngineBase {
   int scalar_grid() const { return (L_.S * 32 + 255) / 256; }
 
   void emit_cg_body(cudaStream_t s, int phase, cudaGraphConditionalHandle cond, int use_cond) {
-    if (sched_fused_) k_cg_spmv<R, true><<<spmv_grid_, kThreads, 0, s>>>(d_);
-    else k_cg_spmv<R, false><<<spmv_grid_, kThreads, 0, s>>>(d_);
+    k_cg_spmv<R><<<spmv_grid_, kThreads, 0, s>>>(d_);
     k_cg_scalar_alpha<R><<<scalar_grid(), 256, 0, s>>>(d_, phase, cond, use_cond);
     k_cg_update<R><<<upd_grid_, kThreads, 0, s>>>(d_);
     k_cg_scalar_beta<R><<<scalar_grid(), 256, 0, s>>>(d_, phase, cond, use_cond);
-    if (!sched_fused_) k_cg_dir<R><<<upd_grid_, kThreads, 0, s>>>(d_);
   }
 
   static std::string tune_cache_path() {
@@ -953,11 +946,12 @@ class Engine final : public EngineBase {
     d_.material = mat_tmp_;
     elements(tmp_xd_, tmp_vd_, st);
     k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr, nullptr);
-    // loop schedules: the best of three rounds of 30 iterations each (bit 2 is decided below)
+    // loop schedules (bit 0: resident or per-entry grid): the best of three rounds of 30
+    // iterations each (bit 2 and above are decided below)
     float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
     const int iters = 30;
     for (int round = 0; round < 3; ++round) {
-      for (int sched = 0; sched < 4; ++sched) {
+      for (int sched = 2; sched < 4; ++sched) {
         set_schedule(sched);
         k_solve_begin<R><<<1, 32, 0, st>>>(d_);
         k_cg_init<R><<<upd_grid_, kThreads, 0, st>>>(d_, d_.bvec);
@@ -972,9 +966,8 @@ class Engine final : public EngineBase {
         best_ms[sched] = std::min(best_ms[sched], ms);
       }
     }
-    int best_s = 0;
-    for (int sched = 1; sched < 4; ++sched)
-      if (best_ms[sched] < best_ms[best_s]) best_s = sched;
+    int best_s = 2;
+    if (best_ms[3] < best_ms[2]) best_s = 3;
     // then whole solves of this system: the loop alone, and the loop handing over to the
     // per-sheet cluster solver at several points (unless the caller fixed the point)
     if (sheet_solver_ok_) {
@@ -1366,8 +1359,7 @@ class Engine final : public EngineBase {
   bool sheet_solver_ok_ = false;      // every sheet fits one cluster
   int handover_ = 1 << 30;            // sheets left when the device loop hands over
   cudaEvent_t fork_ev_ = nullptr;
-  int res_spmv_[2] = {1, 1}, res_upd_ = 1;  // CTAs resident at once (SpMV separate / fused, update)
-  bool sched_fused_ = true;
+  int res_spmv_ = 1, res_upd_ = 1;  // CTAs resident at once (SpMV, update)
   int schedule_ = 3;
   cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
   std::vector<void*> allocs_;

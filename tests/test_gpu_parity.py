@@ -410,15 +410,15 @@ def test_batched_sheets_match_their_own_oracles(oracle_mod):
 @pytest.mark.parametrize("warm", [False, True])
 def test_checkpointing_and_exec_modes_agree(oracle_mod, warm):
     """Checkpoint-and-recompute (C = 3 of 10 steps), the plain host-polled CG and the CG
-    kernel schedules (fused or separate direction update, resident or per-entry grid,
-    with or without the per-sheet cluster solver, and the autotuned one) give bitwise the same
+    kernel schedules (resident or per-entry grid, with or without a per-sheet cluster solver
+    and its on-chip and dense variants, and the autotuned one) give bitwise the same
     trajectory and gradients as the captured-graph run without checkpoints; with
     warm-started solves too (the recompute replays the stored starting vectors)."""
     sheets = sheets_mixed(seed=21)[:2]
     steps, dt = 10, 1 / 30
     res = []
-    for exec_mode, ckpt, sched in (("graph", 0, 3), ("graph", 3, 0), ("plain", 3, 1), ("plain", 0, 2), ("graph", 0, -1),
-                                   ("graph", 3, 6), ("plain", 0, 5), ("graph", 0, 4)):
+    for exec_mode, ckpt, sched in (("graph", 0, 3), ("graph", 3, 2), ("plain", 3, 3), ("plain", 0, 2), ("graph", 0, -1),
+                                   ("graph", 3, 6), ("plain", 0, 7), ("graph", 0, 22), ("plain", 3, 15)):
         b = make_batch(sheets, steps=steps, dt=dt, precision="f32", tol=1e-6, exec_mode=exec_mode, ckpt=ckpt,
                        schedule=sched, warm=warm)
         x0 = to_cuda(np.concatenate([s.rest for s in sheets]), torch.float32)
