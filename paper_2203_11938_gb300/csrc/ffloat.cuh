@@ -50,11 +50,15 @@ __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (do
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 
 // a / b: float quotient, its remainder a - q1 b formed in float-float, one correction term
-// (the double-double division of Hida, Li and Bailey, carried out on float pairs)
+// (the double-double division of Hida, Li and Bailey, carried out on float pairs).  The
+// two partial quotients come from the fast float division (within 2 ulp): the remainder
+// is formed from the q1 actually taken, so the result keeps about 44 bits (relative error
+// <= 6.5e-14 in an emulation over 20,000 quotients, against 1.6e-14 with correctly rounded
+// partial quotients); it sits on the per-iteration serial chain of every CG solve.
 __device__ __forceinline__ FF ff_div(FF a, FF b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float q1 = __fdividef(a.hi, b.hi);
   const FF r = ff_add(a, ff_neg(ff_mul(b, q1)));
-  const float q2 = __fdiv_rn(r.hi, b.hi);
+  const float q2 = __fdividef(r.hi, b.hi);
   const float hi = __fadd_rn(q1, q2);
   return {hi, __fsub_rn(q2, __fsub_rn(hi, q1))};
 }
