@@ -228,6 +228,13 @@ RS_HD void tri_pixel_backward(P2 p, const P2* q, const double* inv, const double
 }
 
 // ---------------------------------------------------------------- one pixel
+// A projected triangle as the per-pixel functions read it: corner image points, inverse
+// depths and texture coordinates.
+struct TriRec {
+  P2 q[3];
+  double inv[3], uv[6];
+};
+
 // Projected corners of every triangle: q [n] image points, inv [n] inverse depths.
 struct Scene {
   const int* tris;    // [m][3]
@@ -239,44 +246,112 @@ struct Scene {
   int Wt, Ht;
 };
 
-RS_HD void corners(const Scene& s, int j, P2* q, double* inv, double* uv) {
+RS_HD TriRec corners(const Scene& s, int j) {
+  TriRec r;
   for (int k = 0; k < 3; ++k) {
     const int v = s.tris[3 * j + k];
-    q[k] = s.q[v];
-    inv[k] = s.inv[v];
-    uv[2 * k] = s.uv[2 * v];
-    uv[2 * k + 1] = s.uv[2 * v + 1];
+    r.q[k] = s.q[v];
+    r.inv[k] = s.inv[v];
+    r.uv[2 * k] = s.uv[2 * v];
+    r.uv[2 * k + 1] = s.uv[2 * v + 1];
   }
+  return r;
 }
 
-// Colour I[3] and silhouette A of the pixel centre p.
+// Screen-space reach of a triangle: beyond R from its bounding box it contributes exactly
+// nothing to any pixel.  There d^2 > R^2 >= 750 SIGMA_R, so exp(d^2 / SIGMA_R) overflows and
+// its coverage D is exactly 0 (its silhouette factor 1 - D exactly 1), and its colour
+// exponent zn / GAMMA + log D <= zn_max / GAMMA - d^2 / SIGMA_R < EPS / GAMMA - 746 lies more
+// than 746 below the blend's largest exponent, so its weight exp(.) underflows to exactly 0.
+// A triangle with a non-finite corner reaches everywhere (its NaN must reach the energy).
+struct TriReach {
+  double x0, y0, x1, y1, r2;  // bounding box of the corners, R^2
+  bool all;
+};
+RS_HD TriReach tri_reach(const TriRec& t) {
+  TriReach b;
+  b.x0 = fmin(t.q[0].x, fmin(t.q[1].x, t.q[2].x));
+  b.x1 = fmax(t.q[0].x, fmax(t.q[1].x, t.q[2].x));
+  b.y0 = fmin(t.q[0].y, fmin(t.q[1].y, t.q[2].y));
+  b.y1 = fmax(t.q[0].y, fmax(t.q[1].y, t.q[2].y));
+  const double zmax = (fmax(t.inv[0], fmax(t.inv[1], t.inv[2])) - 1.0 / Z_FAR) * zn_scale();
+  b.r2 = SIGMA_R * (fmax(zmax - EPS, 0.0) / GAMMA + 750.0);
+  // x - x is 0 exactly for finite x and NaN for infinities and NaNs
+  bool fin = true;
+  for (int k = 0; k < 3; ++k) fin = fin && t.q[k].x - t.q[k].x == 0.0 && t.q[k].y - t.q[k].y == 0.0 &&
+                                    t.inv[k] - t.inv[k] == 0.0;
+  b.all = !fin;
+  return b;
+}
+// true when the triangle may touch a pixel centre in [ax, bx] x [ay, by]
+RS_HD bool reaches(const TriReach& b, double ax, double ay, double bx, double by) {
+  if (b.all) return true;
+  const double dx = fmax(0.0, fmax(b.x0 - bx, ax - b.x1)), dy = fmax(0.0, fmax(b.y0 - by, ay - b.y1));
+  return dx * dx + dy * dy <= b.r2;
+}
+
+// Per-pixel passes over the triangles (each called for the triangles in ascending order):
+// 1. the largest colour exponent, starting from EPS / GAMMA
+RS_HD void pass_top(P2 p, const TriRec& r, const double* tex, int Wt, int Ht, double* top) {
+  TriPix t;
+  tri_pixel(p, r.q, r.inv, r.uv, tex, Wt, Ht, &t);
+  *top = t.logw > *top ? t.logw : *top;
+}
+// 2. the blend's denominator S, numerator acc[3] and the silhouette's product of (1 - D)
+//    (forward), or of its non-zero factors with the count of zero factors (backward)
+struct PixAcc {
+  double S, acc[3], prod;
+  int zeros;
+};
+RS_HD PixAcc pix_acc_begin(double top) { return {exp(EPS / GAMMA - top), {0.0, 0.0, 0.0}, 1.0, 0}; }
+RS_HD void pass_acc(P2 p, const TriRec& r, const double* tex, int Wt, int Ht, double top, bool split_zeros,
+                    PixAcc* a) {
+  TriPix t;
+  tri_pixel(p, r.q, r.inv, r.uv, tex, Wt, Ht, &t);
+  const double w = exp(t.logw - top);
+  a->S += w;
+  for (int k = 0; k < 3; ++k) a->acc[k] += w * t.C[k];
+  if (split_zeros && 1.0 - t.D == 0.0) ++a->zeros;
+  else a->prod *= 1.0 - t.D;
+}
+
+// 3. (backward) one triangle's share of dE/d(corner image points) gq[3] and dE/d(corner
+//    inverse depths) ginv[3], given dE/dI gI[3], dE/dA gA and the pixel's I = acc / S;
+//    returns false (and leaves gq, ginv at 0) where the share is exactly 0 (weight and
+//    coverage both underflowed)
+RS_HD bool pass_grad(P2 p, const TriRec& r, const double* tex, int Wt, int Ht, double top, const PixAcc& a,
+                     const double* I, const double* gI, double gA, P2* gq, double* ginv) {
+  TriPix t;
+  tri_pixel(p, r.q, r.inv, r.uv, tex, Wt, Ht, &t);
+  const double w = exp(t.logw - top);
+  for (int k = 0; k < 3; ++k) {
+    gq[k] = {0.0, 0.0};
+    ginv[k] = 0.0;
+  }
+  if (w == 0.0 && t.D == 0.0) return false;
+  const double S = a.S;
+  const double gw = (gI[0] * (t.C[0] - I[0]) + gI[1] * (t.C[1] - I[1]) + gI[2] * (t.C[2] - I[2])) / S;
+  const double gC[3] = {gI[0] * w / S, gI[1] * w / S, gI[2] * w / S};
+  const double om = 1.0 - t.D;
+  const double others = om == 0.0 ? (a.zeros == 1 ? a.prod : 0.0) : (a.zeros == 0 ? a.prod / om : 0.0);
+  // dw/ds = w (1 - D) (d log sigmoid(s) / ds = 1 - D), dA/ds = others D (1 - D), dw/dzn = w / GAMMA
+  const double gs = (gw * w + gA * others * t.D) * om;
+  const double gzn = gw * w / GAMMA;
+  tri_pixel_backward(p, r.q, r.inv, r.uv, tex, Wt, Ht, t, gs, gzn, gC, gq, ginv);
+  return true;
+}
+
+// Colour I[3] and silhouette A of the pixel centre p over every triangle.
 // The colour weights w_j = D_j exp(zn_j / GAMMA) and the background's exp(EPS / GAMMA) are
 // evaluated relative to the largest of their exponents (zn_j / GAMMA + log D_j and
 // EPS / GAMMA), so a pixel where every D_j underflows keeps the background's weight 1.
 RS_HD void pixel_forward(const Scene& s, P2 p, double* I, double* A) {
   double top = EPS / GAMMA;
-  for (int j = 0; j < s.m; ++j) {
-    P2 q[3];
-    double inv[3], uv[6];
-    corners(s, j, q, inv, uv);
-    TriPix t;
-    tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    top = t.logw > top ? t.logw : top;
-  }
-  double S = exp(EPS / GAMMA - top), acc[3] = {0.0, 0.0, 0.0}, prod = 1.0;
-  for (int j = 0; j < s.m; ++j) {
-    P2 q[3];
-    double inv[3], uv[6];
-    corners(s, j, q, inv, uv);
-    TriPix t;
-    tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    const double w = exp(t.logw - top);
-    S += w;
-    for (int k = 0; k < 3; ++k) acc[k] += w * t.C[k];
-    prod *= 1.0 - t.D;
-  }
-  for (int k = 0; k < 3; ++k) I[k] = acc[k] / S;
-  *A = 1.0 - prod;
+  for (int j = 0; j < s.m; ++j) pass_top(p, corners(s, j), s.tex, s.Wt, s.Ht, &top);
+  PixAcc a = pix_acc_begin(top);
+  for (int j = 0; j < s.m; ++j) pass_acc(p, corners(s, j), s.tex, s.Wt, s.Ht, top, false, &a);
+  for (int k = 0; k < 3; ++k) I[k] = a.acc[k] / a.S;
+  *A = 1.0 - a.prod;
 }
 
 // Backward at one pixel: gI[3] = dE/dI, gA = dE/dA; add(v, gqx, gqy, ginv) receives the
@@ -284,51 +359,15 @@ RS_HD void pixel_forward(const Scene& s, P2 p, double* I, double* A) {
 template <class Add>
 RS_HD void pixel_backward(const Scene& s, P2 p, const double* gI, double gA, Add add) {
   double top = EPS / GAMMA;
+  for (int j = 0; j < s.m; ++j) pass_top(p, corners(s, j), s.tex, s.Wt, s.Ht, &top);
+  PixAcc a = pix_acc_begin(top);
+  for (int j = 0; j < s.m; ++j) pass_acc(p, corners(s, j), s.tex, s.Wt, s.Ht, top, true, &a);
+  const double I[3] = {a.acc[0] / a.S, a.acc[1] / a.S, a.acc[2] / a.S};
+  // per triangle (the largest exponent cancels in I: no gradient through it)
   for (int j = 0; j < s.m; ++j) {
-    P2 q[3];
-    double inv[3], uv[6];
-    corners(s, j, q, inv, uv);
-    TriPix t;
-    tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    top = t.logw > top ? t.logw : top;
-  }
-  // first pass: S, I, the product of the non-zero (1 - D) factors and the zero count
-  double S = exp(EPS / GAMMA - top), acc[3] = {0.0, 0.0, 0.0}, pnz = 1.0;
-  int zeros = 0;
-  for (int j = 0; j < s.m; ++j) {
-    P2 q[3];
-    double inv[3], uv[6];
-    corners(s, j, q, inv, uv);
-    TriPix t;
-    tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    const double w = exp(t.logw - top);
-    S += w;
-    for (int k = 0; k < 3; ++k) acc[k] += w * t.C[k];
-    if (1.0 - t.D == 0.0) ++zeros;
-    else pnz *= 1.0 - t.D;
-  }
-  const double I[3] = {acc[0] / S, acc[1] / S, acc[2] / S};
-  // second pass: per triangle (the largest exponent cancels in I: no gradient through it)
-  for (int j = 0; j < s.m; ++j) {
-    P2 q[3];
-    double inv[3], uv[6];
-    corners(s, j, q, inv, uv);
-    TriPix t;
-    tri_pixel(p, q, inv, uv, s.tex, s.Wt, s.Ht, &t);
-    const double w = exp(t.logw - top);
-    // a triangle whose weight and coverage both underflowed to 0 contributes exactly nothing
-    // here (dE/ds, dE/dzn and its colour share are all 0)
-    if (w == 0.0 && t.D == 0.0) continue;
-    const double gw = (gI[0] * (t.C[0] - I[0]) + gI[1] * (t.C[1] - I[1]) + gI[2] * (t.C[2] - I[2])) / S;
-    const double gC[3] = {gI[0] * w / S, gI[1] * w / S, gI[2] * w / S};
-    const double om = 1.0 - t.D;
-    const double others = om == 0.0 ? (zeros == 1 ? pnz : 0.0) : (zeros == 0 ? pnz / om : 0.0);
-    // dw/ds = w (1 - D) (d log sigmoid(s) / ds = 1 - D), dA/ds = others D (1 - D), dw/dzn = w / GAMMA
-    const double gs = (gw * w + gA * others * t.D) * om;
-    const double gzn = gw * w / GAMMA;
-    P2 gq[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-    double ginv[3] = {0.0, 0.0, 0.0};
-    tri_pixel_backward(p, q, inv, uv, s.tex, s.Wt, s.Ht, t, gs, gzn, gC, gq, ginv);
+    P2 gq[3];
+    double ginv[3];
+    if (!pass_grad(p, corners(s, j), s.tex, s.Wt, s.Ht, top, a, I, gI, gA, gq, ginv)) continue;
     for (int k = 0; k < 3; ++k) add(s.tris[3 * j + k], gq[k].x, gq[k].y, ginv[k]);
   }
 }

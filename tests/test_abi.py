@@ -109,7 +109,7 @@ def test_host_validation_of_the_newer_entry_points(lib):
     assert "out of range" in lib.cloth_last_error().decode()
     assert lib.cloth_image_energy(*args(2, good)) == -1
     # scratch: 12 W H + 15 n doubles and the 3 m triangle indices
-    assert lib.cloth_image_energy_scratch(3, 1, 8, 8) == 8 * (12 * 64 + 15 * 3 + 2)
+    assert lib.cloth_image_energy_scratch(3, 1, 8, 8) == 8 * (12 * 64 + 15 * 3 + 21 * 1 + 2)
 
 
 def test_image_energy_binding_rejects_wrong_shapes_before_any_launch():
