@@ -106,7 +106,7 @@ typedef struct cloth_opts {
                                at most 16 CTAs (the others keep the first variant),
                                bit 4 (with bit 2, without bit 3) = that solver with one
                                256-row work entry per CTA, clusters of up to 16 CTAs
-                               and three CTAs per SM                                  */
+                               and four CTAs per SM                                   */
   int32_t cg_handover;      /* with schedule bit 2: the device loop runs while more than
                                this many sheets are still iterating, then the per-sheet
                                solver finishes them (>= count: no loop at all);
@@ -217,7 +217,8 @@ int cloth_stats(cloth_batch* batch, int64_t* fwd_cg_iters, int64_t* bwd_cg_iters
 
 /* Per-sheet CG iteration counts of the last call of one phase: 0 = the solves of
  * cloth_forward, 1 = the adjoint solves of cloth_backward, 2 = the forward solves
- * cloth_backward recomputed from checkpoints.  max_iters (host [count]): the most
+ * cloth_backward recomputed from checkpoints, 3 = the solves cloth_time_kernel(5) timed
+ * (cleared again when it returns: always 0 here).  max_iters (host [count]): the most
  * iterations one solve of that sheet took; total_iters (host [count]): the sum over
  * its solves.  Either may be NULL.  Synchronises the stream of the last call.
  * Error INVALID_ARG for another phase. */
@@ -233,8 +234,11 @@ int cloth_matrix_info(const cloth_batch* batch, int64_t* rows, int64_t* blocks,
 /* Average device time [ms] of `reps` back-to-back launches of one step kernel on
  * the state left by the last call, timed with CUDA events on `stream`:
  * kernel 0 = CG SpMV with its per-sheet p^T A p reduction, 1 = CG vector update,
- * 2 = assembly, 3 = membrane element kernel, 4 = bending element kernel.
- * Needs a prior cloth_forward; synchronises `stream`. */
+ * 2 = assembly, 3 = membrane element kernel, 4 = bending element kernel, 5 = a whole CG
+ * solve (every sheet to convergence, the schedule in use, from zero) of the system the
+ * last call assembled last, replayed from one captured graph.  Needs a prior
+ * cloth_forward; synchronises `stream`; leaves the solver's scratch (not the handle's
+ * saved states) overwritten. */
 int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* avg_ms,
                       void* stream);
 
@@ -242,7 +246,10 @@ int cloth_time_kernel(cloth_batch* batch, int32_t kernel, int32_t reps, double* 
  * id (compulsory traffic: every input the kernel needs and every output it writes,
  * once; vertex state read once per vertex), for the roofline of that kernel: the SpMV
  * counts the nonzero blocks (9 values + column each) and its vector traffic for the
- * schedule in use.  No device work; error INVALID_ARG for another id. */
+ * schedule in use; kernel 5 counts, for every sheet, its iterations in the last solve
+ * timed as kernel 5 times what kernels 0 and 1 move for its rows (the matrix once per
+ * iteration).  No device work; error INVALID_ARG for another id, or for kernel 5 before
+ * it was timed. */
 int cloth_kernel_bytes(cloth_batch* batch, int32_t kernel, int64_t* bytes);
 
 /* Wind velocity per sheet for the air drag (cloth_opts.air_density > 0): device

@@ -166,8 +166,9 @@ int cloth_stats(cloth_batch* batch, int64_t* fwd, int64_t* bwd, int64_t* rec, in
 
 int cloth_sheet_iterations(cloth_batch* batch, int32_t phase, int32_t* max_iters, int64_t* total_iters) {
   CLOTH_NEED_BATCH("cloth_sheet_iterations");
-  if (phase < 0 || phase > 2) {
-    cloth::set_last_error("cloth_sheet_iterations: phase must be 0 (forward), 1 (adjoint) or 2 (recomputed forward)");
+  if (phase < 0 || phase > 3) {
+    cloth::set_last_error(
+        "cloth_sheet_iterations: phase must be 0 (forward), 1 (adjoint), 2 (recomputed forward) or 3 (timed)");
     return CLOTH_ERR_INVALID_ARG;
   }
   return batch->engine->sheet_iterations(phase, max_iters, total_iters);

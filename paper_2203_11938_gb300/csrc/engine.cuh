@@ -51,7 +51,8 @@ template <class R> struct CGAcc { using T = double; };
 template <> struct CGAcc<float> { using T = FF; };
 template <class R> using acc_t = typename CGAcc<R>::T;
 
-enum Phase { kPhaseForward = 0, kPhaseBackward = 1, kPhaseRecompute = 2 };
+// kPhaseTimed: the solves cloth_time_kernel times (their counts kept apart)
+enum Phase { kPhaseForward = 0, kPhaseBackward = 1, kPhaseRecompute = 2, kPhaseTimed = 3 };
 
 template <class R>
 struct Dev {
@@ -1152,13 +1153,16 @@ template <> struct DvReg<float> {
 // solve and are read through the read-only (L1) path; the gather records written by other
 // CTAs in the previous phase are read through L2 (ld_rec_l2).
 
-// MINB: CTAs per SM the register budget is sized for (3 for the dense one-entry classes,
+// MINB: CTAs per SM the register budget is sized for (4 for the dense one-entry classes,
 // which put several sheets' CTAs on each SM so that one sheet's barrier waits overlap
 // another's work).
 template <class R, int EPC, int MINB = (EPC == 1 ? 2 : 1)>
 __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, const int* __restrict__ sheets, int nsheets,
                                                                    int CL, int phase) {
   namespace cgrp = cooperative_groups;
+  // column indices kept in registers per row: none in the dense classes (their register
+  // budget goes to more CTAs per SM; the indices then come through L1)
+  constexpr int CC = MINB >= 3 ? 1 : kColCache;
   const int cid = blockIdx.x / CL;
   const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
   if (cid >= nsheets) return;               // uniform over the cluster
@@ -1225,7 +1229,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   R beta_r = beta_of<R>(d.cg[s]);
   V3<R> r = {R(0), R(0), R(0)}, z = r, pold = r, Ap = r;
   DvReg<R> x;
-  int K = 0, base = 0, col[kColCache];
+  int K = 0, base = 0, col[CC];
   const int sl_lane = i & 31;
   if (on) {
     r = ld3(d.r, i);
@@ -1238,7 +1242,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
     base = d.slice_base[sl];
   }
 #pragma unroll
-  for (int q = 0; q < kColCache; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
+  for (int q = 0; q < CC; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
   // the sheet's scalars, advanced by thread 0 with the loop's scalar steps (in shared memory:
   // a register copy in every thread would cost ~26 registers per thread)
   __shared__ CGSheet c;
@@ -1257,7 +1261,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
       for (int m = 0; m < 9; ++m) ab[m] = __ldg(a0 + 32 * m);
       V3<R> y = block_mul(ab, pi);
 #pragma unroll
-      for (int q = 1; q <= kColCache; ++q) {
+      for (int q = 1; q <= CC; ++q) {
         if (q < K) {
           const int j = col[q - 1];
           const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
@@ -1269,7 +1273,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
           block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
         }
       }
-      for (int q = kColCache + 1; q < K; ++q) {
+      for (int q = CC + 1; q < K; ++q) {
         const int j = __ldg(d.cols + (base + q) * 32 + sl_lane);
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
         R av[9];

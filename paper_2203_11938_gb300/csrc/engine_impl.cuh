@@ -36,7 +36,7 @@ class Engine final : public EngineBase {
   // a size class of the per-sheet cluster solver: CL CTAs per cluster, EPC work entries per CTA
   struct SheetClass {
     int CL = 1, EPC = 1, offset = 0, n = 0;
-    bool dense = false;  // k_cg_sheet<R, 1, 3>: several CTAs per SM
+    bool dense = false;  // k_cg_sheet<R, 1, 4>: several CTAs per SM
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
   };
@@ -174,9 +174,9 @@ class Engine final : public EngineBase {
     d.part_b = alloc<acc_t<R>>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.part_c = alloc<acc_t<R>>((size_t)d.NW * kWarpsPerEntry, &rc);
     d.active = alloc<int>(1, &rc);
-    d.iter_total = alloc<unsigned long long>(3, &rc);
-    d.body_runs = alloc<unsigned long long>(3, &rc);
-    d.sheet_iters = alloc<unsigned>(6 * (size_t)L_.S, &rc);
+    d.iter_total = alloc<unsigned long long>(4, &rc);
+    d.body_runs = alloc<unsigned long long>(4, &rc);
+    d.sheet_iters = alloc<unsigned>(8 * (size_t)L_.S, &rc);
     d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
     d.gacc_w = alloc<double>(3 * (size_t)L_.S, &rc);
     d.air_density = o_.air_density;
@@ -206,9 +206,9 @@ class Engine final : public EngineBase {
       return rc;
     }
     if (cudaMemset(d.cg, 0, sizeof(CGSheet) * L_.S) != cudaSuccess ||
-        cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
-        cudaMemset(d.body_runs, 0, sizeof(unsigned long long) * 3) != cudaSuccess ||
-        cudaMemset(d.sheet_iters, 0, sizeof(unsigned) * 6 * L_.S) != cudaSuccess ||
+        cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 4) != cudaSuccess ||
+        cudaMemset(d.body_runs, 0, sizeof(unsigned long long) * 4) != cudaSuccess ||
+        cudaMemset(d.sheet_iters, 0, sizeof(unsigned) * 8 * L_.S) != cudaSuccess ||
         cudaEventCreate(&ev0_) != cudaSuccess || cudaEventCreate(&ev1_) != cudaSuccess ||
         cudaMallocHost(&host_active_, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking) != cudaSuccess ||
@@ -411,8 +411,13 @@ class Engine final : public EngineBase {
                // vector and 10 Hessian blocks written; x, v once per row
         *out = E * (20 + 2 * es + 16 + 96 + 90 * es) + rows * 48;
         break;
+      case 5:  // whole CG solve: every iteration of every sheet moves what kernels 0 and 1 move
+               // for that sheet's rows (matrix once per iteration, as a streaming solve reads it)
+        if (timed_solve_bytes_ < 0) return invalid("cloth_kernel_bytes: kernel 5 needs cloth_time_kernel(5) first");
+        *out = timed_solve_bytes_;
+        break;
       default:
-        return invalid("cloth_kernel_bytes: kernel must be 0..4");
+        return invalid("cloth_kernel_bytes: kernel must be 0..5");
     }
     return CLOTH_OK;
   }
@@ -437,7 +442,8 @@ class Engine final : public EngineBase {
         default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
       }
     };
-    if (which < 0 || which > 4) return invalid("cloth_time_kernel: unknown kernel id");
+    if (which < 0 || which > 5) return invalid("cloth_time_kernel: unknown kernel id");
+    if (which == 5) return time_whole_solve(reps, avg_ms, st);
     k_reopen<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_);
     one();  // warm-up
     k_reopen<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_);
@@ -452,6 +458,69 @@ class Engine final : public EngineBase {
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
     CLOTH_CUDA(cudaGetLastError());
     return CLOTH_OK;
+  }
+
+  // Kernel id 5: whole solves of the system the last call assembled last (right-hand side
+  // in bvec), in the schedule in use, captured once and replayed `reps` times; records the
+  // algorithmic bytes of one solve from its per-sheet iteration counts.
+  int time_whole_solve(int reps, double* avg_ms, cudaStream_t st) {
+    CLOTH_CUDA(cudaStreamSynchronize(st));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CLOTH_CUDA(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeRelaxed));
+    const int rc = solve(d_.bvec, kPhaseTimed, cap_stream_, true);
+    const cudaError_t ec = cudaStreamEndCapture(cap_stream_, &g);
+    if (rc != CLOTH_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc != CLOTH_OK) return rc;
+      CLOTH_CUDA(ec);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CLOTH_CUDA(ei);
+    cudaError_t e = cudaGraphLaunch(ge, st);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(ev0_, st);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1_, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1_);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0_, ev1_);
+    cudaGraphExecDestroy(ge);
+    CLOTH_CUDA(e);
+    *avg_ms = ms / reps;
+    // iterations of one solve: the counters of the timed phase hold reps + 1 identical solves
+    std::vector<unsigned> h(2 * (size_t)L_.S);
+    CLOTH_CUDA(cudaMemcpy(h.data(), d_.sheet_iters + 2 * (size_t)kPhaseTimed * L_.S, sizeof(unsigned) * h.size(),
+                          cudaMemcpyDeviceToHost));
+    const int64_t es = sizeof(R);
+    int64_t bytes = 0;
+    for (int s2 = 0; s2 < L_.S; ++s2) {
+      const int64_t rows = L_.sheet_voff[s2 + 1] - L_.sheet_voff[s2];
+      const int64_t per_iter = sheet_nonzero_blocks(s2) * (9 * es + 4) + rows * 4 * 3 * es +
+                               rows * (5 * 3 * es + 9 * es + 48);
+      bytes += (int64_t)(h[2 * s2 + 1] / (unsigned)(reps + 1)) * per_iter;
+    }
+    timed_solve_bytes_ = bytes;
+    k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseTimed);
+    CLOTH_CUDA(cudaGetLastError());
+    return CLOTH_OK;
+  }
+
+  // nonzero 3x3 blocks of one sheet's rows (padding rows count their identity diagonal)
+  int64_t sheet_nonzero_blocks(int s2) const {
+    int64_t nb = 0;
+    for (int i = L_.sheet_voff[s2]; i < L_.sheet_voff[s2 + 1]; ++i) {
+      if (L_.i2u[i] < 0) {
+        ++nb;
+        continue;
+      }
+      const int sl = i / kSlice, lane = i % kSlice;
+      for (int k = 0; k < L_.slice_K[sl]; ++k) {
+        const size_t ent = ((size_t)L_.slice_base[sl] + k) * kSlice + lane;
+        nb += L_.contrib_ptr[ent + 1] > L_.contrib_ptr[ent] ? 1 : 0;
+      }
+    }
+    return nb;
   }
 
   // ---------------------------------------------------------------- losses
@@ -632,7 +701,7 @@ class Engine final : public EngineBase {
 
   // Size classes (CL, EPC) of k_cg_sheet over the given sheets, each listed largest first,
   // with a stream and an event each; the sheet lists go to the device.
-  // dense: one work entry per CTA (cluster of E CTAs for a sheet of E <= 16 entries, three
+  // dense: one work entry per CTA (cluster of E CTAs for a sheet of E <= 16 entries, four
   // CTAs per SM); sheets of more entries take the (8, 4) class.
   int make_classes(const std::vector<int>& sheets, std::vector<SheetClass>* out, const int** dev_lists,
                    std::string* err, bool dense = false) {
@@ -680,9 +749,9 @@ class Engine final : public EngineBase {
     std::vector<SheetClass> cl;
     const int* lists = nullptr;
     CLOTH_TRY(make_classes(all, &cl, &lists, err, true));
-    bool ok = cudaFuncSetAttribute(k_cg_sheet<R, 1, 3>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    bool ok = cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
               cudaSuccess;
-    cudaFuncSetAttribute(k_cg_sheet<R, 1, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxL1);
     for (const auto& c : cl) {
       if (!ok || !c.dense) continue;
@@ -697,7 +766,7 @@ class Engine final : public EngineBase {
       lc.attrs = &at;
       lc.numAttrs = 1;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_cg_sheet<R, 1, 3>, &lc) != cudaSuccess || n < 1) ok = false;
+      if (cudaOccupancyMaxActiveClusters(&n, k_cg_sheet<R, 1, 4>, &lc) != cudaSuccess || n < 1) ok = false;
     }
     cudaGetLastError();
     dense_classes_ = cl;  // destroyed with the engine either way
@@ -1162,7 +1231,7 @@ class Engine final : public EngineBase {
     const int* lists = use_sm_ ? rest_lists_ : use_dense_ ? dense_lists_ : sheet_lists_;
     for (auto& c : set) {
       CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
-      const cudaError_t le = c.dense ? launch_class<1, 3>(c, phase, lists)
+      const cudaError_t le = c.dense ? launch_class<1, 4>(c, phase, lists)
                              : c.EPC == 1 ? launch_class<1>(c, phase, lists)
                              : c.EPC == 2 ? launch_class<2>(c, phase, lists) : launch_class<4>(c, phase, lists);
       CLOTH_CUDA(le);
@@ -1343,6 +1412,7 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr, body_stream_ = nullptr, last_stream_ = nullptr;
   std::vector<CachedGraph> graphs_;
   int64_t launches_ = 0, fixed_fwd_ = 0, fixed_bwd_ = 0;
+  int64_t timed_solve_bytes_ = -1;  // algorithmic bytes of the last solve timed as kernel 5
   int spmv_grid_ = 1, upd_grid_ = 1;  // CTAs of the SpMV and of the other CG row kernels
   std::vector<SheetClass> classes_;  // size classes of the per-sheet cluster solver
   const int* sheet_lists_ = nullptr;  // their sheets, class after class

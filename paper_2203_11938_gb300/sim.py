@@ -315,7 +315,7 @@ class ClothBatch:
                "cloth_matrix_info")
         return {"rows": r.value, "blocks": b.value, "stored_blocks": s.value, "cg_schedule": c.value}
 
-    KERNELS = {"spmv": 0, "cg_update": 1, "assemble": 2, "elem_tri": 3, "elem_hinge": 4}
+    KERNELS = {"spmv": 0, "cg_update": 1, "assemble": 2, "elem_tri": 3, "elem_hinge": 4, "cg_solve": 5}
 
     def time_kernel(self, name, reps=20):
         ms = ctypes.c_double()
