@@ -52,11 +52,15 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="batch256", choices=["batch256", "grid32", "grid100", "grid256"])
+    p.add_argument("--workload", default="batch256", choices=["batch256", "grid32", "grid100", "grid256", "image_hd"],
+                   help="image_hd: the image energy E_p + 0.5 E_s and dE/dx of a 17x17 sheet (512 triangles) in a "
+                        "1920x1080 frame (frames/s), instead of the simulator step")
     p.add_argument("--exec", dest="exec_mode", default="graph", choices=["graph", "plain"])
     p.add_argument("--no-plain-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cg-schedule", type=int, default=-1, help="CG schedule (default: autotuned); for profiling")
+    p.add_argument("--cg-handover", type=int, default=0, help="CG hand-over point (default: autotuned)")
     p.add_argument("--cold-start", action="store_true",
                    help="every CG solve from zero instead of the previous step's solution")
     p.add_argument("--time-steps", type=int, default=0,
@@ -223,7 +227,8 @@ def run_ours(args):
     meshes = [(s.rest, s.tris, s.pinned) for s in wl.sheets]
     b = sim.ClothBatch(meshes, steps=wl.steps, dt=wl.dt, precision=wl.precision, cg_tol=wl.cg_tol,
                        cg_max_iter=wl.cg_max_iter, checkpoint_every=wl.checkpoint_every, exec_mode=args.exec_mode,
-                       cg_warm_start=W.BENCH_CG_WARM_START and not args.cold_start)
+                       cg_warm_start=W.BENCH_CG_WARM_START and not args.cold_start, cg_schedule=args.cg_schedule,
+                       cg_handover=args.cg_handover)
     dev = "cuda"
     mat = torch.tensor(np.stack([s.material for s in wl.sheets]), dtype=dtype, device=dev)
     x0 = torch.tensor(np.concatenate([s.rest for s in wl.sheets]), dtype=dtype, device=dev)
@@ -374,7 +379,7 @@ def run_ours(args):
     log(f"roofline {roofline}")
     # -------------------- the metric's gradient-error clause on the benched batch itself
     grad_check = None
-    if args.workload == "batch256" and rank == 0:
+    if args.workload == "batch256" and rank == 0 and not args.time_steps:
         grad_check = batch_grad_check(b, wl, mat, x0, v0, dtype)
         log(f"grad check {grad_check}")
     # -------------------- plain single-sheet GPU path on a subset of the sheets
@@ -618,10 +623,67 @@ def run_reference(args):
     }))
 
 
+# ----------------------------------------------------------------------------- image energy
+def image_scene(torch):
+    """A 17x17 sheet (512 triangles, about the paper's ~300 vertices) 2 m in front of the
+    camera, filling about 800 px of a 1920x1080 frame, a seeded 64x64 texture, and the frame
+    and mask it renders to in its rest state; the energy is taken at a seeded perturbation."""
+    from paper_2203_11938_gb300 import sim
+
+    rng = np.random.default_rng(3)
+    N = 17
+    rest, tris = W.grid_mesh(N)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    x = rest + np.c_[0.01 * rng.normal(size=(N * N, 2)), 0.03 * rng.normal(size=N * N)]
+    uv = np.c_[rest[:, 0], 1.0 - rest[:, 1]]
+    tex = rng.uniform(0, 1, (64, 64, 3))
+    cam = (1600.0, 0.5, 0.5, 2.0)
+    blank = torch.zeros(1080, 1920, 3, dtype=torch.float64, device="cuda")
+    _, _, img, sil = sim.image_energy(cu(rest), tris, cu(uv), cu(tex), cam, blank, blank[..., 0].contiguous(),
+                                      want_grad=False, want_render=True)
+    return dict(x=cu(x), tris=tris, uv=cu(uv), tex=cu(tex), camera=cam, image=img.contiguous(),
+                mask=(sil > 0.5).double().contiguous())
+
+
+def run_image(args):
+    """Frames per second of cloth_image_energy (E and dE/dx) on the full-HD scene."""
+    import torch
+
+    from paper_2203_11938_gb300 import build as _build
+    from paper_2203_11938_gb300 import sim
+
+    torch.cuda.set_device(0)
+    _build.build()
+    sc = image_scene(torch)
+    for _ in range(max(args.warmup, 1)):
+        E, g, _, _ = sim.image_energy(**sc)
+    torch.cuda.synchronize()
+    if args.steps == 0:
+        return
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        E, g, _, _ = sim.image_energy(**sc)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "image energy E_p + 0.5 E_s with dE/dx, frames/s", "value": 1e3 / ms,
+                      "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded sheet and texture)",
+                      "config": {"workload": "17x17 sheet (289 vertices, 512 triangles) into a 1920x1080 frame, "
+                                             "64x64 texture, soft rasteriser on 16x16 screen tiles"},
+                      "energy": float(E[0]), "finite": bool(torch.isfinite(g).all()), "clocks": clocks}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "image_hd":
+        run_image(args)
     else:
         run_ours(args)
 
