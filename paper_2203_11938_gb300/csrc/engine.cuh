@@ -1160,9 +1160,10 @@ template <class R, int EPC, int MINB = (EPC == 1 ? 2 : 1)>
 __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, const int* __restrict__ sheets, int nsheets,
                                                                    int CL, int phase) {
   namespace cgrp = cooperative_groups;
-  // column indices kept in registers per row: none in the dense classes (their register
-  // budget goes to more CTAs per SM; the indices then come through L1)
-  constexpr int CC = MINB >= 3 ? 1 : kColCache;
+  // column indices kept in registers per row: none in the dense classes and for three or
+  // more entries per CTA (the register budget goes to more rows per SM; the indices then
+  // come through L1)
+  constexpr int CC = (MINB >= 3 || EPC >= 3) ? 1 : kColCache;
   const int cid = blockIdx.x / CL;
   const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
   if (cid >= nsheets) return;               // uniform over the cluster
@@ -1189,37 +1190,38 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   // the sheet's sum of one partial array, in the order of sheet_sum (lane-strided, then a
   // shuffle tree); called by one full warp
   // The sheet's sums of one or two partial arrays, each in the order of sheet_sum
-  // (lane-strided, then a shuffle tree); every partial is loaded before the first add, so
-  // the (distributed) shared memory loads overlap.  Called by one full warp.
-  constexpr int kPerLane = EPC == 4 ? 8 : 4;  // partials per lane: a class holds at most 16 (EPC <= 2) or 32 entries
+  // (lane-strided, then a shuffle tree); the partials are loaded four at a time before they
+  // are added, so the (distributed) shared memory loads overlap.  Called by one full warp.
   auto sheet_totals = [&](int wa, int wb, acc_t<R>* ta, acc_t<R>* tb) {
-    acc_t<R> va[kPerLane], vb[kPerLane];
     const int q0 = w0 * kWarpsPerEntry, q1 = w1 * kWarpsPerEntry;
-#pragma unroll
-    for (int u = 0; u < kPerLane; ++u) {
-      const int q = q0 + lane + 32 * u;
-      va[u] = acc_zero<R>();
-      vb[u] = acc_zero<R>();
-      if (q < q1) {
-        const int e = q / kWarpsPerEntry - w0, pw = q % kWarpsPerEntry;
-        const int rk = e % CL, jj = e / CL;
-        const acc_t<R>* sa = &sp[wa][jj][pw];
-        const acc_t<R>* sb = &sp[wb][jj][pw];
-        if (CL > 1) {
-          sa = cgrp::this_cluster().map_shared_rank(sa, rk);
-          sb = cgrp::this_cluster().map_shared_rank(sb, rk);
-        }
-        va[u] = *sa;
-        if (tb) vb[u] = *sb;
-      }
-    }
     acc_t<R> a = acc_zero<R>(), b = acc_zero<R>();
+    for (int qb = q0 + lane; qb < q1; qb += 128) {
+      acc_t<R> va[4], vb[4];
 #pragma unroll
-    for (int u = 0; u < kPerLane; ++u)
-      if (q0 + lane + 32 * u < q1) {
-        a = acc_add(a, va[u]);
-        b = acc_add(b, vb[u]);
+      for (int u = 0; u < 4; ++u) {
+        const int q = qb + 32 * u;
+        va[u] = acc_zero<R>();
+        vb[u] = acc_zero<R>();
+        if (q < q1) {
+          const int e = q / kWarpsPerEntry - w0, pw = q % kWarpsPerEntry;
+          const int rk = e % CL, jj = e / CL;
+          const acc_t<R>* sa = &sp[wa][jj][pw];
+          const acc_t<R>* sb = &sp[wb][jj][pw];
+          if (CL > 1) {
+            sa = cgrp::this_cluster().map_shared_rank(sa, rk);
+            sb = cgrp::this_cluster().map_shared_rank(sb, rk);
+          }
+          va[u] = *sa;
+          if (tb) vb[u] = *sb;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (qb + 32 * u < q1) {
+          a = acc_add(a, va[u]);
+          b = acc_add(b, vb[u]);
+        }
+    }
     *ta = acc_warp_total(a);
     if (tb) *tb = acc_warp_total(b);
   };

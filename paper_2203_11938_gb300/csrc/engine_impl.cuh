@@ -235,9 +235,13 @@ class Engine final : public EngineBase {
     // shared memory of at most 16 CTAs also get a partition for the on-chip solver
     // (k_cg_sheet_sm)
     {
+      // clusters of 16 CTAs (a non-portable size): 2 entries per CTA for sheets of 17-32
+      // entries, 3 (without the register cache) for 33-48, where the device can launch them
+      wide2_ok_ = wide_cluster_ok(k_cg_sheet<R, 2>, 2 * kThreads);
+      wide3_ok_ = wide_cluster_ok(k_cg_sheet<R, 3>, 3 * kThreads);
       int max_entries = 0;
       for (int s2 = 0; s2 < L_.S; ++s2) max_entries = std::max(max_entries, L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2]);
-      sheet_solver_ok_ = max_entries <= 32;
+      sheet_solver_ok_ = max_entries <= (wide3_ok_ ? 48 : 32);
       if (sheet_solver_ok_) {
         std::vector<int> all(L_.S);
         for (int s2 = 0; s2 < L_.S; ++s2) all[s2] = s2;
@@ -250,6 +254,7 @@ class Engine final : public EngineBase {
         // which holds the matrix rows it rereads every iteration
         cudaFuncSetAttribute(k_cg_sheet<R, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         cudaFuncSetAttribute(k_cg_sheet<R, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
+        cudaFuncSetAttribute(k_cg_sheet<R, 3>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         cudaFuncSetAttribute(k_cg_sheet<R, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
           *err = "CUDA setup failed";
@@ -715,7 +720,9 @@ class Engine final : public EngineBase {
       else if (E <= 4) CL = 2, EPC = 2;
       else if (E <= 8) CL = 4, EPC = 2;
       else if (E <= 16) CL = 8, EPC = 2;
-      else CL = 8, EPC = 4;
+      else if (E <= 32 && wide2_ok_) CL = 16, EPC = 2;
+      else if (E <= 32) CL = 8, EPC = 4;
+      else CL = 16, EPC = 3;  // E <= 48 (wide3_ok_ checked by the caller)
       cls[{CL, EPC}].push_back(s2);
     }
     std::vector<int> lists;
@@ -742,6 +749,29 @@ class Engine final : public EngineBase {
     *dev_lists = lists.empty() ? nullptr : upload(lists, &rc);
     if (rc != CLOTH_OK) *err = "device allocation failed";
     return rc;
+  }
+
+  // true when one cluster of 16 CTAs of `threads` threads of `kern` can be resident
+  template <class K>
+  bool wide_cluster_ok(K kern, int threads) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(16);
+    lc.blockDim = dim3((unsigned)threads);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 16;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    lc.attrs = &at;
+    lc.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, kern, &lc) == cudaSuccess && n >= 1;
+    cudaGetLastError();
+    return ok;
   }
 
   // Dense classes (schedule bit 4), kept only if every cluster shape can be launched.
@@ -1233,7 +1263,8 @@ class Engine final : public EngineBase {
       CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
       const cudaError_t le = c.dense ? launch_class<1, 4>(c, phase, lists)
                              : c.EPC == 1 ? launch_class<1>(c, phase, lists)
-                             : c.EPC == 2 ? launch_class<2>(c, phase, lists) : launch_class<4>(c, phase, lists);
+                             : c.EPC == 2 ? launch_class<2>(c, phase, lists)
+                             : c.EPC == 3 ? launch_class<3>(c, phase, lists) : launch_class<4>(c, phase, lists);
       CLOTH_CUDA(le);
       CLOTH_CUDA(cudaEventRecord(c.done, c.stream));
       CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
@@ -1427,6 +1458,7 @@ class Engine final : public EngineBase {
   const int* dense_lists_ = nullptr;
   bool dense_ok_ = false, use_dense_ = false;
   bool sheet_solver_ok_ = false;      // every sheet fits one cluster
+  bool wide2_ok_ = false, wide3_ok_ = false;  // 16-CTA clusters of 2 or 3 entries per CTA launchable
   int handover_ = 1 << 30;            // sheets left when the device loop hands over
   cudaEvent_t fork_ev_ = nullptr;
   int res_spmv_ = 1, res_upd_ = 1;  // CTAs resident at once (SpMV, update)

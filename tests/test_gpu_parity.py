@@ -444,13 +444,14 @@ def test_sheet_solver_matches_device_loop_bitwise(precision):
     """The per-sheet cluster solver (schedule bit 2) and its on-chip variant (bit 3: matrix
     and gathered vectors in the shared memory of up to 16 CTAs, neighbours read through
     distributed shared memory) and its dense classes (bit 4: one work entry per CTA, several
-    CTAs per SM) against the device loop alone, on sheets of 1 to 20 work entries (every
-    cluster size and entries-per-CTA class; in FP64 the largest sheets do not fit on chip
-    and take the first solver): bitwise the same trajectory, gradients and per-sheet
-    iteration counts, in graph and plain execution."""
+    CTAs per SM) against the device loop alone, on sheets of 1 to 40 work entries (every
+    cluster size and entries-per-CTA class, including the 16-CTA clusters of 2 and 3 entries
+    per CTA; in FP64 the largest sheets do not fit on chip and take the first solver):
+    bitwise the same trajectory, gradients and per-sheet iteration counts, in graph and
+    plain execution."""
     rng = np.random.Generator(np.random.PCG64(8))
     sheets = []
-    for N in (16, 20, 30, 40, 50, 64, 70):
+    for N in (16, 20, 30, 40, 50, 64, 70, 100):
         rest, tris = W.grid_mesh(N)
         sheets.append(W.Sheet(N, rest, tris, W.pins(N, "top2"), W.sample_material(rng), None))
     dtype = torch.float32 if precision == "f32" else torch.float64
