@@ -1120,6 +1120,11 @@ __global__ void k_cg_scalar_beta(Dev<R> d, int phase, cudaGraphConditionalHandle
 // order, so all take the same branches.  The arithmetic and the summation orders are those
 // of the device loop above, so the results are bitwise the same.
 constexpr int kColCache = 16;  // column indices kept in registers per row (further slots are loaded)
+constexpr int kSmemCols = 12;  // off-diagonal column indices per row kept in shared memory, classes without
+                               // the register cache (a grid sheet's interior rows have 12: 6 edge and
+                               // 6 hinge neighbours)
+constexpr int kSmemColsWide = 8;  // the same for four entries per CTA (static shared memory stays < 48 KB)
+constexpr int kColSmemCarveout = 50;  // percent of the SM's shared storage given to shared memory there
 
 // CG solution of one row in registers: FP64, or float-float in FP32 mode
 template <class R> struct DvReg {
@@ -1161,9 +1166,11 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
                                                                    int CL, int phase) {
   namespace cgrp = cooperative_groups;
   // column indices kept in registers per row: none in the dense classes and for three or
-  // more entries per CTA (the register budget goes to more rows per SM; the indices then
-  // come through L1)
-  constexpr int CC = (MINB >= 3 || EPC >= 3) ? 1 : kColCache;
+  // more entries per CTA (the register budget goes to more rows per SM); those keep the
+  // first SC off-diagonal indices of each row in shared memory instead, so that a gather
+  // waits on one L2 access (the neighbour's record) rather than two
+  constexpr int CC = (MINB >= 3 || EPC >= 3) ? 0 : kColCache;
+  constexpr int SC = CC > 0 ? 0 : EPC >= 4 ? kSmemColsWide : kSmemCols;
   const int cid = blockIdx.x / CL;
   const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
   if (cid >= nsheets) return;               // uniform over the cluster
@@ -1175,6 +1182,11 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   __shared__ acc_t<R> bc_alpha;
   __shared__ R bc_beta;
   __shared__ int bc_stop;
+  __shared__ int scol[SC > 0 ? SC : 1][kThreads * EPC];  // [slot - 1][thread]
+  // the dense classes also keep each row's block-Jacobi inverse in shared memory (the
+  // update phase then makes no global load)
+  constexpr bool SD = MINB >= 3;
+  __shared__ R sdinv[SD ? 9 : 1][SD ? kThreads * EPC : 1];
 
   const int jl = threadIdx.x / kThreads, t = threadIdx.x - jl * kThreads;
   const int lane = threadIdx.x & 31, wp = t >> 5;
@@ -1231,7 +1243,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   R beta_r = beta_of<R>(d.cg[s]);
   V3<R> r = {R(0), R(0), R(0)}, z = r, pold = r, Ap = r;
   DvReg<R> x;
-  int K = 0, base = 0, col[CC];
+  int K = 0, base = 0, col[CC > 0 ? CC : 1];
   const int sl_lane = i & 31;
   if (on) {
     r = ld3(d.r, i);
@@ -1245,6 +1257,14 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   }
 #pragma unroll
   for (int q = 0; q < CC; ++q) col[q] = (on && q + 1 < K) ? d.cols[(base + q + 1) * 32 + sl_lane] : 0;
+  // each thread reads back only its own row's entries: no barrier needed
+#pragma unroll
+  for (int q = 0; q < SC; ++q)
+    if (on && q + 1 < K) scol[q][threadIdx.x] = __ldg(d.cols + (base + q + 1) * 32 + sl_lane);
+  if (SD && on) {
+#pragma unroll
+    for (int m = 0; m < 9; ++m) sdinv[m][SD ? threadIdx.x : 0] = __ldg(d.dinv + (size_t)m * d.Np + i);
+  }
   // the sheet's scalars, advanced by thread 0 with the loop's scalar steps (in shared memory:
   // a register copy in every thread would cost ~26 registers per thread)
   __shared__ CGSheet c;
@@ -1275,8 +1295,28 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
           block_acc(y, av, V3<R>{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z});
         }
       }
-      for (int q = CC + 1; q < K; ++q) {
-        const int j = __ldg(d.cols + (base + q) * 32 + sl_lane);
+      // two slots per trip: both slots' blocks and neighbour records are requested before
+      // either is used, so two L2 round trips overlap (accumulation order unchanged)
+      auto col_of = [&](int q) {
+        return q <= SC ? scol[q - 1][threadIdx.x] : __ldg(d.cols + (base + q) * 32 + sl_lane);
+      };
+      int q = CC + 1;
+      for (; q + 1 < K; q += 2) {
+        const int j0 = col_of(q), j1 = col_of(q + 1);
+        const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
+        R av[9], bv[9];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) {
+          av[m] = __ldg(a + 32 * m);
+          bv[m] = __ldg(a + 32 * 9 + 32 * m);
+        }
+        const Rec<R> n0 = ld_rec_l2(rec(d, k, j0)), n1 = ld_rec_l2(rec(d, k, j1));
+        const V3<R> p0 = next_dir(n0.z, beta_r, n0.p), p1 = next_dir(n1.z, beta_r, n1.p);
+        block_acc(y, av, V3<R>{p0.x - pi.x, p0.y - pi.y, p0.z - pi.z});
+        block_acc(y, bv, V3<R>{p1.x - pi.x, p1.y - pi.y, p1.z - pi.z});
+      }
+      if (q < K) {
+        const int j = col_of(q);
         const R* a = d.Aval + (size_t)(base + q) * 32 * 9 + sl_lane;
         R av[9];
 #pragma unroll
@@ -1313,7 +1353,7 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
       {
         R dm[9];
 #pragma unroll
-        for (int m = 0; m < 9; ++m) dm[m] = __ldg(d.dinv + (size_t)m * d.Np + i);
+        for (int m = 0; m < 9; ++m) dm[m] = SD ? sdinv[m][SD ? threadIdx.x : 0] : __ldg(d.dinv + (size_t)m * d.Np + i);
         z = block_mul(dm, r);  // = apply_dinv
       }
       st_rec_z(rec(d, k + 1, i), z);  // gathered by the neighbours in the next iteration

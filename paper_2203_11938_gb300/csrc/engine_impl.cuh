@@ -250,12 +250,13 @@ class Engine final : public EngineBase {
         CLOTH_TRY(make_sm_classes(&rest, err));
         CLOTH_TRY(make_classes(rest, &rest_classes_, &rest_lists_, err));
         CLOTH_TRY(make_dense_classes(all, err));
-        // the kernel needs little shared memory: leave the rest of the SM's storage to L1,
-        // which holds the matrix rows it rereads every iteration
+        // the classes with the register column cache need little shared memory: leave the
+        // rest of the SM's storage to L1, which holds the matrix rows they reread every
+        // iteration; the others keep column indices in shared memory (up to 37 KB per CTA)
         cudaFuncSetAttribute(k_cg_sheet<R, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
         cudaFuncSetAttribute(k_cg_sheet<R, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
-        cudaFuncSetAttribute(k_cg_sheet<R, 3>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
-        cudaFuncSetAttribute(k_cg_sheet<R, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
+        cudaFuncSetAttribute(k_cg_sheet<R, 3>, cudaFuncAttributePreferredSharedMemoryCarveout, kColSmemCarveout);
+        cudaFuncSetAttribute(k_cg_sheet<R, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, kColSmemCarveout);
         if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
           *err = "CUDA setup failed";
           return CLOTH_ERR_CUDA;
@@ -781,8 +782,8 @@ class Engine final : public EngineBase {
     CLOTH_TRY(make_classes(all, &cl, &lists, err, true));
     bool ok = cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
               cudaSuccess;
-    cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxL1);
+    // four CTAs per SM, each with ~13 KB of column indices in shared memory
+    cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, kColSmemCarveout);
     for (const auto& c : cl) {
       if (!ok || !c.dense) continue;
       cudaLaunchConfig_t lc = {};
