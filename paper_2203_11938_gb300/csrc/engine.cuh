@@ -89,6 +89,7 @@ struct Dev {
   unsigned long long* iter_total;
   unsigned long long* body_runs;  // [3] CG loop-body executions per phase
   unsigned* sheet_iters;          // [3][S][2] per phase and sheet: largest solve, sum over solves
+  unsigned* last_iters;           // [S] iterations of each sheet's last finished solve
   double* gacc;  // [S][3] dL/dY, dL/dkb, dL/drho
   double* gacc_w;  // [S][3] dL/dw (wind velocity)
   double* row_w;   // [Np][3] per-vertex shares of dL/dw (adjoint scratch)
@@ -377,6 +378,7 @@ __device__ __forceinline__ void finish_sheet(const Dev<R>& d, int s, int phase, 
   unsigned* si = d.sheet_iters + 2 * ((size_t)phase * d.S + s);
   si[0] = max(si[0], (unsigned)d.cg[s].iters);
   si[1] += (unsigned)d.cg[s].iters;
+  d.last_iters[s] = (unsigned)d.cg[s].iters;
   const int left = atomicSub(d.active, 1) - 1;
   // exactly one thread sees each value of `left`: the one reaching the hand-over point
   // ends the device loop (the per-sheet cluster solver finishes the remaining sheets)
@@ -1119,6 +1121,35 @@ __global__ void k_cg_scalar_beta(Dev<R> d, int phase, cudaGraphConditionalHandle
 // Every CTA forms alpha, beta and the stopping test from the same partial sums in the same
 // order, so all take the same branches.  The arithmetic and the summation orders are those
 // of the device loop above, so the results are bitwise the same.
+// Launch order of the per-sheet solver's clusters.  The hardware starts a launch's clusters
+// roughly in index order, and a solve ends with its slowest sheet, so each size class's
+// sheets are put in order of the iterations their last finished solve took, most first
+// (ties keep the class's own order): the sheets that run longest start first.  A rank sort
+// in one CTA per class (seg: the classes' offsets into the lists, then the total); a class
+// of more than kOrderMax sheets keeps its own order.  The order changes no sheet's
+// arithmetic, only when its cluster runs.
+constexpr int kOrderMax = 2048;
+template <class R>
+__global__ void k_order_lists(Dev<R> d, const int* __restrict__ seg, const int* __restrict__ base,
+                              int* __restrict__ order) {
+  __shared__ unsigned key[kOrderMax];
+  const int c0 = seg[blockIdx.x], n = seg[blockIdx.x + 1] - c0;
+  const int* b = base + c0;
+  int* o = order + c0;
+  if (n > kOrderMax) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) o[q] = b[q];
+    return;
+  }
+  for (int q = threadIdx.x; q < n; q += blockDim.x) key[q] = d.last_iters[b[q]];
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const unsigned kq = key[q];
+    int rank = 0;
+    for (int u = 0; u < n; ++u) rank += (key[u] > kq || (key[u] == kq && u < q)) ? 1 : 0;
+    o[rank] = b[q];
+  }
+}
+
 constexpr int kColCache = 16;  // column indices kept in registers per row (further slots are loaded)
 constexpr int kSmemCols = 12;  // off-diagonal column indices per row kept in shared memory, classes without
                                // the register cache (a grid sheet's interior rows have 12: 6 edge and

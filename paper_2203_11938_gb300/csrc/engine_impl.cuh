@@ -177,6 +177,7 @@ class Engine final : public EngineBase {
     d.iter_total = alloc<unsigned long long>(4, &rc);
     d.body_runs = alloc<unsigned long long>(4, &rc);
     d.sheet_iters = alloc<unsigned>(8 * (size_t)L_.S, &rc);
+    d.last_iters = alloc<unsigned>(L_.S, &rc);
     d.gacc = alloc<double>(3 * (size_t)L_.S, &rc);
     d.gacc_w = alloc<double>(3 * (size_t)L_.S, &rc);
     d.air_density = o_.air_density;
@@ -209,6 +210,7 @@ class Engine final : public EngineBase {
         cudaMemset(d.iter_total, 0, sizeof(unsigned long long) * 4) != cudaSuccess ||
         cudaMemset(d.body_runs, 0, sizeof(unsigned long long) * 4) != cudaSuccess ||
         cudaMemset(d.sheet_iters, 0, sizeof(unsigned) * 8 * L_.S) != cudaSuccess ||
+        cudaMemset(d.last_iters, 0, sizeof(unsigned) * L_.S) != cudaSuccess ||
         cudaEventCreate(&ev0_) != cudaSuccess || cudaEventCreate(&ev1_) != cudaSuccess ||
         cudaMallocHost(&host_active_, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking) != cudaSuccess ||
@@ -748,6 +750,21 @@ class Engine final : public EngineBase {
     }
     int rc = CLOTH_OK;
     *dev_lists = lists.empty() ? nullptr : upload(lists, &rc);
+    if (!lists.empty() && rc == CLOTH_OK) {
+      // the classes' offsets and the total, for the launch-order kernel, and its output
+      std::vector<int> seg;
+      int off = 0;
+      for (auto& kv : cls) {
+        seg.push_back(off);
+        off += (int)kv.second.size();
+      }
+      seg.push_back(off);
+      ListOrder lo;
+      lo.seg = upload(seg, &rc);
+      lo.order = alloc<int>(lists.size(), &rc);
+      lo.nclasses = (int)cls.size();
+      orders_[*dev_lists] = lo;
+    }
     if (rc != CLOTH_OK) *err = "device allocation failed";
     return rc;
   }
@@ -1249,6 +1266,15 @@ class Engine final : public EngineBase {
 
   int emit_tail(cudaStream_t st, int phase) {
     if (d_.tail_threshold <= 0) return CLOTH_OK;
+    auto& set = use_sm_ ? rest_classes_ : use_dense_ ? dense_classes_ : classes_;
+    const int* lists = use_sm_ ? rest_lists_ : use_dense_ ? dense_lists_ : sheet_lists_;
+    // the classes' sheets in launch order, longest last solve first
+    auto lo = orders_.find(lists);
+    if (lo != orders_.end()) {
+      launch(k_order_lists<R>, dim3(lo->second.nclasses), dim3(256), st, d_, lo->second.seg, lists,
+             lo->second.order);
+      lists = lo->second.order;
+    }
     CLOTH_CUDA(cudaEventRecord(fork_ev_, st));
     if (use_sm_) {
       for (auto& c : sm_classes_) {
@@ -1258,8 +1284,6 @@ class Engine final : public EngineBase {
         CLOTH_CUDA(cudaStreamWaitEvent(st, c.done, 0));
       }
     }
-    auto& set = use_sm_ ? rest_classes_ : use_dense_ ? dense_classes_ : classes_;
-    const int* lists = use_sm_ ? rest_lists_ : use_dense_ ? dense_lists_ : sheet_lists_;
     for (auto& c : set) {
       CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
       const cudaError_t le = c.dense ? launch_class<1, 4>(c, phase, lists)
@@ -1448,6 +1472,12 @@ class Engine final : public EngineBase {
   int spmv_grid_ = 1, upd_grid_ = 1;  // CTAs of the SpMV and of the other CG row kernels
   std::vector<SheetClass> classes_;  // size classes of the per-sheet cluster solver
   const int* sheet_lists_ = nullptr;  // their sheets, class after class
+  struct ListOrder {
+    const int* seg = nullptr;  // [classes + 1] offsets of the classes in the list
+    int* order = nullptr;      // the list in launch order (k_order_lists)
+    int nclasses = 0;
+  };
+  std::map<const int*, ListOrder> orders_;  // by class list
   // on-chip solver: its size classes (one cluster size each), their partitions, and the
   // k_cg_sheet classes of the sheets it cannot hold
   std::vector<SmClass> sm_classes_;
