@@ -6,6 +6,8 @@
 // tri_reach); the others map one thread to one pixel (or one vertex) and move the data.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <string>
 
 #include "engine.h"
@@ -103,15 +105,22 @@ __global__ void __launch_bounds__(kPix) k_render(Scene s, const TriRec* __restri
 }
 
 // one pass of the separable Gaussian filter (dir 0: along rows, 1: along columns)
+// (the 2r + 1 taps are formed once per CTA, by the same function, into shared memory)
 __global__ void k_blur(int W, int H, int dir, double norm, const double* __restrict__ src, double* __restrict__ dst) {
+  constexpr int kMaxTaps = 2 * 32 + 1;
+  static_assert(3.0 * SIGMA_S <= 32.0 && kPix >= kMaxTaps, "radius up to 32 px, one thread per tap");
+  __shared__ double tap[kMaxTaps];
+  const int r = blur_radius();
+  if ((int)threadIdx.x <= 2 * r) tap[threadIdx.x] = blur_tap((int)threadIdx.x - r, norm);
+  __syncthreads();
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= W * H) return;
-  const int u = pix % W, v = pix / W, r = blur_radius();
+  const int u = pix % W, v = pix / W;
   double acc = 0.0;
   for (int k = -r; k <= r; ++k) {
     const int uu = dir == 0 ? u + k : u, vv = dir == 0 ? v : v + k;
     if (uu < 0 || uu >= W || vv < 0 || vv >= H) continue;
-    acc += blur_tap(k, norm) * src[(size_t)vv * W + uu];
+    acc += tap[k + r] * src[(size_t)vv * W + uu];
   }
   dst[pix] = acc;
 }
@@ -126,18 +135,25 @@ __global__ void k_sil(int n, const double* __restrict__ ga, const double* __rest
   sg[pix] = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
 }
 
-// E = sum ep + LAMBDA sum es, in a fixed order (one CTA)
-__global__ void k_energy(int n, const double* __restrict__ ep, const double* __restrict__ es, double* __restrict__ E) {
+// Sums of a[i] + lam b[i] (b may be null): CTA c sums its contiguous chunk of [0, n)
+// (thread-strided, then a shared-memory tree) into out[c].  E = sum ep + LAMBDA sum es takes
+// two launches, one partial per CTA and then one CTA over the partials: a fixed order, so
+// the energy is deterministic.
+constexpr int kEnergyParts = 1024;
+__global__ void k_energy_sum(int n, const double* __restrict__ a, const double* __restrict__ b, double lam,
+                             double* __restrict__ out) {
   __shared__ double sh[kPix];
+  const int chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
   double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += ep[i] + LAMBDA * es[i];
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += b ? a[i] + lam * b[i] : a[i];
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *E = sh[0];
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
 // dE/d(image point, inverse depth) of every vertex: the passes of pixel_backward over the
@@ -286,7 +302,10 @@ extern "C" int cloth_image_energy(int32_t n, int32_t m, const int32_t* tris, con
   k_blur<<<gp, kPix, 0, st>>>(W, H, 0, norm, mask, tmp);
   k_blur<<<gp, kPix, 0, st>>>(W, H, 1, norm, tmp, gb);
   k_sil<<<gp, kPix, 0, st>>>((int)WH, ga, gb, es, sg);
-  k_energy<<<1, kPix, 0, st>>>((int)WH, ep, es, energy);
+  // the partials go to tmp, which the filter passes below overwrite only after this
+  const int parts = (int)std::min<size_t>(kEnergyParts, (WH + kPix - 1) / kPix);
+  k_energy_sum<<<parts, kPix, 0, st>>>((int)WH, ep, es, LAMBDA, tmp);
+  k_energy_sum<<<1, kPix, 0, st>>>(parts, tmp, nullptr, 0.0, energy);
   if (dE_dx) {
     // the filter is symmetric with zero padding, so its adjoint is the same filter
     k_blur<<<gp, kPix, 0, st>>>(W, H, 0, norm, sg, tmp);
