@@ -93,14 +93,18 @@ typedef struct cloth_opts {
                                or CLOTH_PRECOND_BLOCK_JACOBI (3x3 block per vertex)   */
   int32_t cg_schedule;      /* CG kernel schedule, all with bitwise-identical results:
                                -1 = autotune at cloth_batch_create (times each schedule
-                               on the batch's matrix, caches the choice in the JSON file
-                               $CLOTH_TUNE_CACHE or ~/.cache/cloth_sim/tune.json);
+                               on the batch's matrix, and the element kernels at 64,
+                               128 and 256 threads per CTA; caches the choice in the
+                               JSON file $CLOTH_TUNE_CACHE or
+                               ~/.cache/cloth_sim/tune.json); an explicit schedule
+                               keeps 128 threads per CTA for the element kernels;
                                0..31: bit 1 is always set (the direction update is
                                folded into the SpMV; a value without it means the same),
                                bit 0 = resident-CTA grid looping over rows, bit 2 =
                                per-sheet cluster solver for the sheets still iterating
                                at the hand-over point (every sheet of at most 8192
-                               vertices gets one thread-block cluster), bit 3 (with
+                               vertices, or 12288 where clusters of 16 CTAs can be
+                               launched, gets one thread-block cluster), bit 3 (with
                                bit 2) = the on-chip variant of that solver for every
                                sheet whose matrix and vectors fit the shared memory of
                                at most 16 CTAs (the others keep the first variant),

@@ -570,9 +570,10 @@ __device__ __forceinline__ void load_relative_d(const double* __restrict__ x, co
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const double* __restrict__ x,
-                                                          const double* __restrict__ v) {
+// NT: threads per CTA (the autotuner picks 64, 128 or 256 per element kind)
+template <class R, int NT = kElemThreads>
+__global__ void __launch_bounds__(NT) k_elem_tri(Dev<R> d, const double* __restrict__ x,
+                                                 const double* __restrict__ v) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.M) return;
   TriConst<R> k = tri_const(d, t);
@@ -608,9 +609,9 @@ __global__ void __launch_bounds__(kElemThreads) k_elem_tri(Dev<R> d, const doubl
     for (int q = 0; q < 9; ++q) ho[9 * b + q] = H[b][q];
 }
 
-template <class R>
-__global__ void __launch_bounds__(kElemThreads) k_elem_hinge(Dev<R> d, const double* __restrict__ x,
-                                                            const double* __restrict__ v) {
+template <class R, int NT = kElemThreads>
+__global__ void __launch_bounds__(NT) k_elem_hinge(Dev<R> d, const double* __restrict__ x,
+                                                   const double* __restrict__ v) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   HingeConst<R> k = hinge_const(d, e);

@@ -438,7 +438,6 @@ class Engine final : public EngineBase {
     if (!have_forward_ || reps < 1 || !avg_ms) return invalid("cloth_time_kernel: needs a forward and reps >= 1");
     cudaStream_t st = (cudaStream_t)stream_;
     d_.material = mat_;
-    const int gm = (L_.M + kElemThreads - 1) / kElemThreads, ge = (L_.E + kElemThreads - 1) / kElemThreads;
     auto one = [&]() {
       switch (which) {
         case 0:
@@ -446,8 +445,8 @@ class Engine final : public EngineBase {
           break;
         case 1: k_cg_update<R><<<upd_grid_, kThreads, 0, st>>>(d_); break;
         case 2: k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr, nullptr); break;
-        case 3: k_elem_tri<R><<<gm, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
-        default: if (L_.E) k_elem_hinge<R><<<ge, kElemThreads, 0, st>>>(d_, sx(0), sv(0)); break;
+        case 3: elements_of(0, sx(0), sv(0), st); break;
+        default: elements_of(1, sx(0), sv(0), st); break;
       }
     };
     if (which < 0 || which > 5) return invalid("cloth_time_kernel: unknown kernel id");
@@ -691,11 +690,53 @@ class Engine final : public EngineBase {
 
   // element forces and Hessian blocks at x; with v, the stored element vectors are f - h H~ v
   void elements(const double* x, const double* v, cudaStream_t st) {
-    if (L_.M)
-      launch(k_elem_tri<R>, dim3((L_.M + kElemThreads - 1) / kElemThreads), dim3(kElemThreads), st, d_, x, v);
-    if (L_.E)
-      launch(k_elem_hinge<R>, dim3((L_.E + kElemThreads - 1) / kElemThreads), dim3(kElemThreads), st, d_, x, v);
+    elements_of(0, x, v, st);
+    elements_of(1, x, v, st);
   }
+  // the membrane (kind 0) or bending (kind 1) element kernel at its tuned block size
+  void elements_of(int kind, const double* x, const double* v, cudaStream_t st) {
+    const int n = kind == 0 ? L_.M : L_.E, nt = kind == 0 ? tri_nt_ : hin_nt_;
+    if (!n) return;
+    const dim3 g((unsigned)((n + nt - 1) / nt)), b((unsigned)nt);
+    if (kind == 0) {
+      if (nt == 64) launch(k_elem_tri<R, 64>, g, b, st, d_, x, v);
+      else if (nt == 256) launch(k_elem_tri<R, 256>, g, b, st, d_, x, v);
+      else launch(k_elem_tri<R, 128>, g, b, st, d_, x, v);
+    } else {
+      if (nt == 64) launch(k_elem_hinge<R, 64>, g, b, st, d_, x, v);
+      else if (nt == 256) launch(k_elem_hinge<R, 256>, g, b, st, d_, x, v);
+      else launch(k_elem_hinge<R, 128>, g, b, st, d_, x, v);
+    }
+  }
+  // Block sizes of the element kernels (64, 128 or 256 threads per CTA), per element kind:
+  // the fastest in three rounds of five launches on the state the autotuner set up.
+  int tune_element_shapes(cudaStream_t st) {
+    for (int kind = 0; kind < 2; ++kind) {
+      if ((kind == 0 ? L_.M : L_.E) == 0) continue;
+      int& nt = kind == 0 ? tri_nt_ : hin_nt_;
+      float best = 1e30f;
+      int best_nt = kElemThreads;
+      for (int round = 0; round < 3; ++round)
+        for (int c : {128, 64, 256}) {
+          nt = c;
+          elements_of(kind, tmp_xd_, tmp_vd_, st);  // warm-up
+          CLOTH_CUDA(cudaEventRecord(ev0_, st));
+          for (int k = 0; k < 5; ++k) elements_of(kind, tmp_xd_, tmp_vd_, st);
+          CLOTH_CUDA(cudaEventRecord(ev1_, st));
+          CLOTH_CUDA(cudaEventSynchronize(ev1_));
+          float ms = 0.f;
+          CLOTH_CUDA(cudaEventElapsedTime(&ms, ev0_, ev1_));
+          if (ms < best) {
+            best = ms;
+            best_nt = c;
+          }
+        }
+      nt = best_nt;
+    }
+    return CLOTH_OK;
+  }
+  static int nt_code(int nt) { return nt == 64 ? 1 : nt == 256 ? 2 : 0; }
+  static int nt_of(int code) { return code == 1 ? 64 : code == 2 ? 256 : kElemThreads; }
 
   int assemble_at(const void* x, const void* v, const void* F, cudaStream_t st) {
     gather_state((const R*)x, tmp_xd_, st);
@@ -1039,13 +1080,16 @@ class Engine final : public EngineBase {
     }
     std::ostringstream key;
     key << prop.name << "|" << (sizeof(R) == 4 ? "f32" : "f64") << "|rows=" << L_.Np << "|entries=" << d_.NW
-        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover << "|v3";
+        << "|slots=" << L_.total_slots() << "|sheets=" << L_.S << "|handover=" << o_.cg_handover << "|v4";
     const std::string path = tune_cache_path();
     auto cache = path.empty() ? std::map<std::string, int>() : read_tune_cache(path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-      // value: schedule (bits 0-4) + 32 x hand-over point
-      if (o_.cg_handover == 0 && (it->second >> 5) > 0) handover_ = it->second >> 5;
+      // value: schedule (bits 0-4), membrane and bending block-size codes (bits 5-6, 7-8),
+      // hand-over point (bits 9 and up)
+      if (o_.cg_handover == 0 && (it->second >> 9) > 0) handover_ = it->second >> 9;
+      tri_nt_ = nt_of((it->second >> 5) & 3);
+      hin_nt_ = nt_of((it->second >> 7) & 3);
       set_schedule(it->second & 31);
       return CLOTH_OK;
     }
@@ -1061,6 +1105,7 @@ class Engine final : public EngineBase {
     CLOTH_CUDA(cudaMemcpy(tmp_xd_, L_.rest.data(), sizeof(double) * L_.rest.size(), cudaMemcpyHostToDevice));
     CLOTH_CUDA(cudaMemset(tmp_vd_, 0, sizeof(double) * n3()));
     d_.material = mat_tmp_;
+    CLOTH_TRY(tune_element_shapes(st));
     elements(tmp_xd_, tmp_vd_, st);
     k_assemble<R><<<d_.NW, kThreads, 0, st>>>(d_, nullptr, nullptr);
     // loop schedules (bit 0: resident or per-entry grid): the best of three rounds of 30
@@ -1126,7 +1171,7 @@ class Engine final : public EngineBase {
     k_reset_status<R><<<(L_.S + 255) / 256, 256, 0, st>>>(d_, kPhaseForward);
     CLOTH_CUDA(cudaStreamSynchronize(st));
     if (!path.empty()) {
-      cache[key.str()] = best_s | ((best_s & 4) ? handover_ << 5 : 0);
+      cache[key.str()] = best_s | nt_code(tri_nt_) << 5 | nt_code(hin_nt_) << 7 | ((best_s & 4) ? handover_ << 9 : 0);
       write_tune_cache(path, cache);
     }
     return CLOTH_OK;
@@ -1489,6 +1534,7 @@ class Engine final : public EngineBase {
   const int* dense_lists_ = nullptr;
   bool dense_ok_ = false, use_dense_ = false;
   bool sheet_solver_ok_ = false;      // every sheet fits one cluster
+  int tri_nt_ = kElemThreads, hin_nt_ = kElemThreads;  // element kernels' block sizes (autotuned)
   bool wide2_ok_ = false, wide3_ok_ = false;  // 16-CTA clusters of 2 or 3 entries per CTA launchable
   int handover_ = 1 << 30;            // sheets left when the device loop hands over
   cudaEvent_t fork_ev_ = nullptr;
