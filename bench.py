@@ -367,8 +367,8 @@ def run_ours(args):
     # matrix once per iteration), over the solve's device time.
     cg = kernels["cg_solve"]
     achieved = cg["algorithmic_bytes"] / (cg["avg_launch_ms"] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "CG solve: per-sheet cluster solver k_cg_sheet (dense classes: one 256-row "
-                "work entry per CTA, a cluster per sheet), every sheet to convergence",
+    roofline = {"bound": "hbm", "kernel": "CG solve: per-sheet cluster solver k_cg_sheet (dense classes: two 256-row "
+                "work entries per CTA, two CTAs per SM, a cluster per sheet), every sheet to convergence",
                 "cg_schedule": mi["cg_schedule"],
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": committed_traffic("cg_solve"), "peak_source": peak_kind,

@@ -108,9 +108,9 @@ typedef struct cloth_opts {
                                bit 2) = the on-chip variant of that solver for every
                                sheet whose matrix and vectors fit the shared memory of
                                at most 16 CTAs (the others keep the first variant),
-                               bit 4 (with bit 2, without bit 3) = that solver with one
-                               256-row work entry per CTA, clusters of up to 16 CTAs
-                               and four CTAs per SM                                   */
+                               bit 4 (with bit 2, without bit 3) = that solver with two
+                               256-row work entries per CTA, clusters of up to 8 CTAs
+                               and two CTAs per SM                                    */
   int32_t cg_handover;      /* with schedule bit 2: the device loop runs while more than
                                this many sheets are still iterating, then the per-sheet
                                solver finishes them (>= count: no loop at all);

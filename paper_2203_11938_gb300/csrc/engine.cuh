@@ -1190,18 +1190,18 @@ template <> struct DvReg<float> {
 // solve and are read through the read-only (L1) path; the gather records written by other
 // CTAs in the previous phase are read through L2 (ld_rec_l2).
 
-// MINB: CTAs per SM the register budget is sized for (4 for the dense one-entry classes,
-// which put several sheets' CTAs on each SM so that one sheet's barrier waits overlap
-// another's work).
+// MINB: CTAs per SM the register budget is sized for (2 for the dense classes of two
+// entries per CTA, which put two sheets' CTAs on each SM so that one sheet's barrier waits
+// overlap another's work).
 template <class R, int EPC, int MINB = (EPC == 1 ? 2 : 1)>
 __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, const int* __restrict__ sheets, int nsheets,
                                                                    int CL, int phase) {
   namespace cgrp = cooperative_groups;
-  // column indices kept in registers per row: none in the dense classes and for three or
-  // more entries per CTA (the register budget goes to more rows per SM); those keep the
-  // first SC off-diagonal indices of each row in shared memory instead, so that a gather
-  // waits on one L2 access (the neighbour's record) rather than two
-  constexpr int CC = (MINB >= 3 || EPC >= 3) ? 0 : kColCache;
+  // column indices kept in registers per row: only where the launch leaves 128 registers
+  // per thread (fewer than 768 threads per SM); the others (the dense classes, three or
+  // more entries per CTA) keep the first SC off-diagonal indices of each row in shared
+  // memory, so that a gather waits on one L2 access (the neighbour's record) rather than two
+  constexpr int CC = EPC * MINB >= 3 ? 0 : kColCache;
   constexpr int SC = CC > 0 ? 0 : EPC >= 4 ? kSmemColsWide : kSmemCols;
   const int cid = blockIdx.x / CL;
   const int rank = blockIdx.x - cid * CL;  // = the CTA's rank in its (1-D) cluster
@@ -1216,8 +1216,9 @@ __global__ void __launch_bounds__(kThreads * EPC, MINB) k_cg_sheet(Dev<R> d, con
   __shared__ int bc_stop;
   __shared__ int scol[SC > 0 ? SC : 1][kThreads * EPC];  // [slot - 1][thread]
   // the dense classes also keep each row's block-Jacobi inverse in shared memory (the
-  // update phase then makes no global load)
-  constexpr bool SD = MINB >= 3;
+  // update phase then makes no global load; FP32 only: in FP64 the static shared memory
+  // would pass 48 KB)
+  constexpr bool SD = EPC * MINB >= 4 && EPC <= 2 && sizeof(R) == 4;
   __shared__ R sdinv[SD ? 9 : 1][SD ? kThreads * EPC : 1];
 
   const int jl = threadIdx.x / kThreads, t = threadIdx.x - jl * kThreads;

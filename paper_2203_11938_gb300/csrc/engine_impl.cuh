@@ -36,7 +36,7 @@ class Engine final : public EngineBase {
   // a size class of the per-sheet cluster solver: CL CTAs per cluster, EPC work entries per CTA
   struct SheetClass {
     int CL = 1, EPC = 1, offset = 0, n = 0;
-    bool dense = false;  // k_cg_sheet<R, 1, 4>: several CTAs per SM
+    bool dense = false;  // k_cg_sheet<R, 2, 2>: two CTAs of two entries per SM
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
   };
@@ -758,7 +758,7 @@ class Engine final : public EngineBase {
     for (int s2 : sheets) {
       const int E = L_.sheet_wfirst[s2 + 1] - L_.sheet_wfirst[s2];
       int CL = 1, EPC = 1;
-      if (dense && E <= 16) CL = E, EPC = 1;
+      if (dense && E <= 16) CL = (E + 1) / 2, EPC = 2;
       else if (E <= 1) CL = 1, EPC = 1;
       else if (E <= 2) CL = 1, EPC = 2;
       else if (E <= 4) CL = 2, EPC = 2;
@@ -778,7 +778,7 @@ class Engine final : public EngineBase {
       SheetClass c;
       c.CL = kv.first.first;
       c.EPC = kv.first.second;
-      c.dense = dense && c.EPC == 1;
+      c.dense = dense && c.EPC == 2 && c.CL <= 8;
       c.offset = (int)lists.size();
       c.n = (int)v.size();
       lists.insert(lists.end(), v.begin(), v.end());
@@ -838,15 +838,15 @@ class Engine final : public EngineBase {
     std::vector<SheetClass> cl;
     const int* lists = nullptr;
     CLOTH_TRY(make_classes(all, &cl, &lists, err, true));
-    bool ok = cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-              cudaSuccess;
-    // four CTAs per SM, each with ~13 KB of column indices in shared memory
-    cudaFuncSetAttribute(k_cg_sheet<R, 1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, kColSmemCarveout);
+    // two CTAs per SM, each with ~25 KB of column indices (and in FP32 ~18 KB of
+    // block-Jacobi inverses) in shared memory; clusters of at most 8 CTAs
+    bool ok = cudaFuncSetAttribute(k_cg_sheet<R, 2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   kColSmemCarveout) == cudaSuccess;
     for (const auto& c : cl) {
       if (!ok || !c.dense) continue;
       cudaLaunchConfig_t lc = {};
       lc.gridDim = dim3((unsigned)c.CL);
-      lc.blockDim = dim3(kThreads);
+      lc.blockDim = dim3(2 * kThreads);
       cudaLaunchAttribute at;
       at.id = cudaLaunchAttributeClusterDimension;
       at.val.clusterDim.x = (unsigned)c.CL;
@@ -855,7 +855,7 @@ class Engine final : public EngineBase {
       lc.attrs = &at;
       lc.numAttrs = 1;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_cg_sheet<R, 1, 4>, &lc) != cudaSuccess || n < 1) ok = false;
+      if (cudaOccupancyMaxActiveClusters(&n, k_cg_sheet<R, 2, 2>, &lc) != cudaSuccess || n < 1) ok = false;
     }
     cudaGetLastError();
     dense_classes_ = cl;  // destroyed with the engine either way
@@ -1331,7 +1331,7 @@ class Engine final : public EngineBase {
     }
     for (auto& c : set) {
       CLOTH_CUDA(cudaStreamWaitEvent(c.stream, fork_ev_, 0));
-      const cudaError_t le = c.dense ? launch_class<1, 4>(c, phase, lists)
+      const cudaError_t le = c.dense ? launch_class<2, 2>(c, phase, lists)
                              : c.EPC == 1 ? launch_class<1>(c, phase, lists)
                              : c.EPC == 2 ? launch_class<2>(c, phase, lists)
                              : c.EPC == 3 ? launch_class<3>(c, phase, lists) : launch_class<4>(c, phase, lists);
