@@ -570,6 +570,22 @@ __device__ __forceinline__ void load_relative_d(const double* __restrict__ x, co
   }
 }
 
+// N values of v to p with 8-byte stores (p 8-byte aligned, N even: the element records
+// of 54 and 90 FP32 values, 216 and 360 bytes) or, in FP64, 16-byte stores (p 16-byte
+// aligned)
+template <int N>
+__device__ __forceinline__ void st_record(float* p, const float* v) {
+  static_assert(N % 2 == 0, "record size");
+#pragma unroll
+  for (int c = 0; c < N / 2; ++c) reinterpret_cast<float2*>(p)[c] = make_float2(v[2 * c], v[2 * c + 1]);
+}
+template <int N>
+__device__ __forceinline__ void st_record(double* p, const double* v) {
+  static_assert(N % 2 == 0, "record size");
+#pragma unroll
+  for (int c = 0; c < N / 2; ++c) reinterpret_cast<double2*>(p)[c] = make_double2(v[2 * c], v[2 * c + 1]);
+}
+
 // NT: threads per CTA (the autotuner picks 64, 128 or 256 per element kind)
 template <class R, int NT = kElemThreads>
 __global__ void __launch_bounds__(NT) k_elem_tri(Dev<R> d, const double* __restrict__ x,
@@ -602,11 +618,7 @@ __global__ void __launch_bounds__(NT) k_elem_tri(Dev<R> d, const double* __restr
     fo[3 * a + 1] = fd[a].y;
     fo[3 * a + 2] = fd[a].z;
   }
-  R* ho = d.tri_H + 54 * (size_t)t;
-#pragma unroll
-  for (int b = 0; b < 6; ++b)
-#pragma unroll
-    for (int q = 0; q < 9; ++q) ho[9 * b + q] = H[b][q];
+  st_record<54>(d.tri_H + 54 * (size_t)t, &H[0][0]);
 }
 
 template <class R, int NT = kElemThreads>
@@ -633,18 +645,12 @@ __global__ void __launch_bounds__(NT) k_elem_hinge(Dev<R> d, const double* __res
 #pragma unroll
     for (int a = 0; a < 4; ++a) fd[a] = {fd[a].x - h * Hv[a].x, fd[a].y - h * Hv[a].y, fd[a].z - h * Hv[a].z};
   }
-  double* fo = d.hin_f + 12 * (size_t)e;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    fo[3 * a] = fd[a].x;
-    fo[3 * a + 1] = fd[a].y;
-    fo[3 * a + 2] = fd[a].z;
+  {  // 12 FP64 force entries (96 bytes per hinge, 16-byte aligned)
+    const double fv[12] = {fd[0].x, fd[0].y, fd[0].z, fd[1].x, fd[1].y, fd[1].z,
+                           fd[2].x, fd[2].y, fd[2].z, fd[3].x, fd[3].y, fd[3].z};
+    st_record<12>(d.hin_f + 12 * (size_t)e, fv);
   }
-  R* ho = d.hin_H + 90 * (size_t)e;
-#pragma unroll
-  for (int b = 0; b < 10; ++b)
-#pragma unroll
-    for (int q = 0; q < 9; ++q) ho[9 * b + q] = H[b][q];
+  st_record<90>(d.hin_H + 90 * (size_t)e, &H[0][0]);
 }
 
 // element-vertex force slot -> pointer to 3 reals
