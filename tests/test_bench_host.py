@@ -31,6 +31,10 @@ def test_measured_peak_reads_the_peaks_file(tmp_path, monkeypatch):
 def test_committed_traffic_is_the_summary_line():
     t = bench.committed_traffic()
     assert t is not None and 2.0e8 < t < 2.5e8  # one full-matrix SpMV launch of the batch
+    # the roofline kernel of the line: one whole CG solve of the batch (129.6 GB of
+    # algorithmic bytes, mostly served from L2)
+    w = bench.committed_traffic("cg_solve")
+    assert w is not None and 1.0e8 < w < 1.296e11
 
 
 def test_command_line_defaults(monkeypatch):
