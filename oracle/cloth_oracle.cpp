@@ -422,6 +422,32 @@ void inv3(const double m[9], double out[9]) {
   out[8] = (m[0] * m[4] - m[1] * m[3]) / det;
 }
 
+// The same matrix as flat row arrays (columns ascending, as the map iterates), made once
+// per solve: its product sums every row in the same order as Sparse::matvec, so every
+// result is identical; it only spares walking the maps in each CG iteration.
+struct Csr {
+  std::vector<size_t> ptr;
+  std::vector<int> col;
+  std::vector<double> val;
+  explicit Csr(const Sparse& A) : ptr(A.rows.size() + 1, 0) {
+    for (size_t i = 0; i < A.rows.size(); ++i) ptr[i + 1] = ptr[i] + A.rows[i].size();
+    col.reserve(ptr.back());
+    val.reserve(ptr.back());
+    for (const auto& row : A.rows)
+      for (const auto& kv : row) {
+        col.push_back(kv.first);
+        val.push_back(kv.second);
+      }
+  }
+  void matvec(const std::vector<double>& p, std::vector<double>& y) const {
+    for (size_t i = 0; i + 1 < ptr.size(); ++i) {
+      double s = 0.0;
+      for (size_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * p[col[q]];
+      y[i] = s;
+    }
+  }
+};
+
 // Jacobi-preconditioned CG on A y = rhs from y = 0, stopping when
 // |r|_2 <= tol |rhs|_2 (checked before each iteration) or after max_iter.
 // precond 0: scalar Jacobi z_i = r_i / A_ii;  1: block Jacobi with the 3x3 diagonal
@@ -430,6 +456,7 @@ void inv3(const double m[9], double out[9]) {
 int pcg(const Sparse& A, const std::vector<double>& rhs, double tol, int max_iter, int precond, std::vector<double>& y,
         int* iters) {
   const size_t N = rhs.size();
+  const Csr C(A);
   std::vector<double> r(rhs), z(N), p(N), Ap(N), dinv(N), binv(precond ? 3 * N : 0);
   y.assign(N, 0.0);
   if (precond) {
@@ -469,7 +496,7 @@ int pcg(const Sparse& A, const std::vector<double>& rhs, double tol, int max_ite
   double rr = dotv(r, r);
   for (int k = 0; k < max_iter; ++k) {
     if (std::sqrt(rr) <= tol * bnorm) return 0;
-    A.matvec(p, Ap);
+    C.matvec(p, Ap);
     double pAp = dotv(p, Ap);
     if (!std::isfinite(pAp)) return 3;
     if (pAp <= 0.0) return 2;
