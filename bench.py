@@ -376,6 +376,10 @@ def run_ours(args):
                 "launch": "one whole solve (every size class of the solver, one captured graph)",
                 "bytes_per_row_iteration": round((kernels["spmv"]["algorithmic_bytes"] +
                                                   kernels["cg_update"]["algorithmic_bytes"]) / mi["rows"], 1)}
+    # DRAM traffic against the algorithmic bytes: far below 1, the solve's rows are served
+    # from L2, so `achieved` is an effective bandwidth and the bound is iteration latency
+    if roofline["traffic"] and cg["algorithmic_bytes"] > 0:
+        roofline["traffic_share_of_algorithmic"] = round(roofline["traffic"] / cg["algorithmic_bytes"], 4)
     log(f"roofline {roofline}")
     # -------------------- the metric's gradient-error clause on the benched batch itself
     grad_check = None

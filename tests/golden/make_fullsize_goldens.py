@@ -15,10 +15,11 @@ FP32 path receives them, and stores the values the GPU tests compare entry by en
       segment) with the smooth wind; loss = pinhole reprojection against the template's
       tracks (workloads.template_tracks); oracle CG tol 1e-9.
   grid256_segment
-      the 256 x 256 sheet with four corners pinned, its first 4 steps with the smooth wind
-      (the oracle needs about 20 minutes per solve at this size); loss
-      L = sum_{t>=1} |x_t - X|^2; oracle CG tol 1e-8.  Per-vertex arrays are stored for
-      every 5th vertex (all norms are of the full arrays).
+      the 256 x 256 sheet with four corners pinned, its first 20 steps (the workload's
+      first checkpoint segment) with the smooth wind (the oracle needs about 75 s per
+      solve at this size); loss L = sum_{t>=1} |x_t - X|^2; oracle CG tol 1e-8.
+      Per-vertex arrays are stored for every 5th vertex (all norms are of the full
+      arrays).
 
 Run: python tests/golden/make_fullsize_goldens.py [case ...]   (hours of CPU time; each
 case runs in its own process, all cases in parallel).
@@ -38,10 +39,8 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 CASES = ("batch_largest", "batch_slowest", "grid100_segment", "grid256_segment")
-# The oracle's map-per-row sparse matrix needs about 20 minutes per solve of the 65,536-vertex
-# sheet, so its stored run covers the first 4 steps (forward and adjoint), not a whole
-# 20-step checkpoint segment.
-GRID256_STEPS = 4
+# the 256 x 256 workload checkpoints every 20 steps: its stored run is one whole segment
+GRID256_STEPS = 20
 
 
 def f32r(a):
