@@ -14,6 +14,9 @@ FP32 path receives them, and stores the values the GPU tests compare entry by en
       the 100 x 100 sheet of the pinhole workload, its first 30 steps (one checkpoint
       segment) with the smooth wind; loss = pinhole reprojection against the template's
       tracks (workloads.template_tracks); oracle CG tol 1e-9.
+  grid100_full
+      the same sheet over the workload's whole trajectory (300 steps, ten checkpoint
+      segments of 30); loss and tolerance as above.
   grid256_segment
       the 256 x 256 sheet with four corners pinned, its first 20 steps (the workload's
       first checkpoint segment) with the smooth wind (the oracle needs about 75 s per
@@ -38,7 +41,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-CASES = ("batch_largest", "batch_slowest", "grid100_segment", "grid256_segment")
+CASES = ("batch_largest", "batch_slowest", "grid100_segment", "grid100_full", "grid256_segment")
 # the 256 x 256 workload checkpoints every 20 steps: its stored run is one whole segment
 GRID256_STEPS = 20
 
@@ -60,6 +63,11 @@ def _case_inputs(case):
         s = cfg.sheets[0]
         return dict(sheet=s, index=0, steps=30, dt=cfg.dt, forces=s.forces[:30], loss="pinhole", tol=1e-9,
                     stride=1, camera=cfg.camera)
+    if case == "grid100_full":
+        cfg = W.config3()
+        s = cfg.sheets[0]
+        return dict(sheet=s, index=0, steps=cfg.steps, dt=cfg.dt, forces=s.forces[:cfg.steps], loss="pinhole",
+                    tol=1e-9, stride=1, camera=cfg.camera)
     if case == "grid256_segment":
         cfg = W.config5(steps=GRID256_STEPS)
         s = cfg.sheets[0]

@@ -131,6 +131,15 @@ def test_grid100_first_segment_matches_stored_oracle():
     _single_sheet_case("grid100_segment", cfg, 30, 10, "pinhole")
 
 
+def test_grid100_whole_trajectory_matches_stored_oracle():
+    """The 100 x 100 pinhole workload's whole trajectory (300 steps of 1/30 s, smooth wind,
+    FP32, CG tol 1e-6, the workload's checkpoints every 30 steps: the backward recomputes
+    nine segments) with the pinhole loss against the template's tracks, against the
+    oracle's 300-step run at tol 1e-9."""
+    cfg = W.config3()
+    _single_sheet_case("grid100_full", cfg, cfg.steps, cfg.checkpoint_every, "pinhole")
+
+
 def test_grid256_first_segment_matches_stored_oracle():
     """The 256 x 256 four-corner workload's first checkpoint segment (20 steps of 1/60 s,
     smooth wind, FP32, CG tol 1e-6, recompute every 5 steps) with L = sum |x_t - X|^2,
