@@ -217,6 +217,10 @@ def template_tracks(rest, steps, scale=250.0, centre=(0.5, 0.5)):
 # values: the largest grid (64 x 64) and the one the FP64 oracle needs the most CG
 # iterations for (61 x 61, the largest Y (N - 1)^2 / rho of the batch).
 BATCH_GOLDEN_SHEETS = {"largest": 93, "slowest": 220}
+# further sheets of the batch with stored oracle values, one for each of several size
+# classes of the per-sheet solver (grid sides 16-56: clusters of 1 to 7 CTAs in the dense
+# classes; the largest sheet's is 8), compared by the full-size GPU test
+BATCH_GOLDEN_CLASSES = {"n16": 139, "n22": 4, "n30": 5, "n38": 22, "n42": 14, "n46": 66, "n54": 157, "n56": 15}
 
 # Solver setting of the benchmark runs (and of the full-size parity tests of the same
 # configuration): every CG solve starts from zero, as the oracle's does.  (Warm starts save

@@ -10,6 +10,9 @@ FP32 path receives them, and stores the values the GPU tests compare entry by en
       sheets 93 (64 x 64) and 220 (61 x 61) of the 256-sheet batch (seed 1), 100 steps of
       1/30 s, two top corners pinned, no external force; loss L = sum_{t>=1} |x_t - X|^2
       (X: the template); oracle CG tol 1e-10.
+  batch_n16, batch_n22, batch_n30, batch_n38, batch_n42, batch_n46, batch_n54, batch_n56
+      one sheet of each of those grid sides from the same batch (workloads.
+      BATCH_GOLDEN_CLASSES), the same run.
   grid100_segment
       the 100 x 100 sheet of the pinhole workload, its first 30 steps (one checkpoint
       segment) with the smooth wind; loss = pinhole reprojection against the template's
@@ -41,7 +44,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-CASES = ("batch_largest", "batch_slowest", "grid100_segment", "grid100_full", "grid256_segment")
+CASES = ("batch_largest", "batch_slowest", "batch_n16", "batch_n22", "batch_n30", "batch_n38", "batch_n42",
+         "batch_n46", "batch_n54", "batch_n56", "grid100_segment", "grid100_full", "grid256_segment")
 # the 256 x 256 workload checkpoints every 20 steps: its stored run is one whole segment
 GRID256_STEPS = 20
 
@@ -55,7 +59,8 @@ def _case_inputs(case):
 
     if case.startswith("batch_"):
         cfg = W.config4()
-        k = W.BATCH_GOLDEN_SHEETS[case.split("_", 1)[1]]
+        name = case.split("_", 1)[1]
+        k = W.BATCH_GOLDEN_SHEETS.get(name, W.BATCH_GOLDEN_CLASSES.get(name))
         s = cfg.sheets[k]
         return dict(sheet=s, index=k, steps=cfg.steps, dt=cfg.dt, forces=None, loss="l2", tol=1e-10, stride=1)
     if case == "grid100_segment":

@@ -67,12 +67,15 @@ def _check_sheet(g, x_mid, x_final, v_final, gm, gx0, gv0, gF=None, what=""):
     return {"x_final": err_x, "material": max(abs(gm[q] / g["g_material"][q] - 1) for q in (0, 2, 3))}
 
 
-def test_batch256_largest_and_slowest_sheets_match_stored_oracle():
+def test_batch256_sampled_sheets_match_stored_oracle():
     """The whole 256-sheet batch (100 steps, FP32, CG tol 1e-7) with the loss
-    L = sum_{t>=1} |x_t - X|^2; its largest sheet (64 x 64) and the sheet the oracle needs
-    the most CG iterations for (61 x 61) against the oracle's 100-step run at tol 1e-10."""
+    L = sum_{t>=1} |x_t - X|^2; its largest sheet (64 x 64), the sheet the oracle needs the
+    most CG iterations for (61 x 61) and one sheet of each of the grid sides 16, 22, 30,
+    38, 42, 46, 54 and 56 (with the largest, every cluster size the dense classes form, 1
+    to 8 CTAs) against the oracle's 100-step runs at tol 1e-10."""
     cfg = W.config4()
-    gold = {k: _golden(f"batch_{k}") for k in W.BATCH_GOLDEN_SHEETS}
+    sampled = dict(W.BATCH_GOLDEN_SHEETS, **W.BATCH_GOLDEN_CLASSES)
+    gold = {k: _golden(f"batch_{k}") for k in sampled}
     f32 = torch.float32
     b = make_batch(cfg.sheets, steps=cfg.steps, dt=cfg.dt, precision="f32", tol=cfg.cg_tol, max_iter=cfg.cg_max_iter,
                    warm=BENCH_WARM)
@@ -88,7 +91,7 @@ def test_batch256_largest_and_slowest_sheets_match_stored_oracle():
     gx0 = split(to_np(g["x0"]), b.sheet_sizes)
     gv0 = split(to_np(g["v0"]), b.sheet_sizes)
     gm = to_np(g["material"])
-    for name, k in W.BATCH_GOLDEN_SHEETS.items():
+    for name, k in sampled.items():
         gd = gold[name]
         assert int(gd["sheet_index"]) == k and int(gd["steps"]) == T
         v_final = (xs[k][T] - xs[k][T - 1]) / cfg.dt
