@@ -26,6 +26,8 @@ FP32 path receives them, and stores the values the GPU tests compare entry by en
       solve at this size); loss L = sum_{t>=1} |x_t - X|^2; oracle CG tol 1e-8.
       Per-vertex arrays are stored for every 5th vertex (all norms are of the full
       arrays).
+  grid256_two_segments
+      the same over its first two checkpoint segments (40 steps).
 
 Run: python tests/golden/make_fullsize_goldens.py [case ...]   (hours of CPU time; each
 case runs in its own process, all cases in parallel).
@@ -45,7 +47,8 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 CASES = ("batch_largest", "batch_slowest", "batch_n16", "batch_n22", "batch_n30", "batch_n38", "batch_n42",
-         "batch_n46", "batch_n54", "batch_n56", "grid100_segment", "grid100_full", "grid256_segment")
+         "batch_n46", "batch_n54", "batch_n56", "grid100_segment", "grid100_full", "grid256_segment",
+         "grid256_two_segments")
 # the 256 x 256 workload checkpoints every 20 steps: its stored run is one whole segment
 GRID256_STEPS = 20
 
@@ -73,10 +76,11 @@ def _case_inputs(case):
         s = cfg.sheets[0]
         return dict(sheet=s, index=0, steps=cfg.steps, dt=cfg.dt, forces=s.forces[:cfg.steps], loss="pinhole",
                     tol=1e-9, stride=1, camera=cfg.camera)
-    if case == "grid256_segment":
-        cfg = W.config5(steps=GRID256_STEPS)
+    if case.startswith("grid256_"):
+        T = GRID256_STEPS if case == "grid256_segment" else 2 * GRID256_STEPS
+        cfg = W.config5(steps=T)
         s = cfg.sheets[0]
-        return dict(sheet=s, index=0, steps=GRID256_STEPS, dt=cfg.dt, forces=s.forces[:GRID256_STEPS], loss="l2",
+        return dict(sheet=s, index=0, steps=T, dt=cfg.dt, forces=s.forces[:T], loss="l2",
                     tol=1e-8, stride=5)
     raise ValueError(case)
 
