@@ -150,3 +150,12 @@ def test_grid256_first_segment_matches_stored_oracle():
     cfg = W.config5()
     steps = int(_golden("grid256_segment")["steps"])
     _single_sheet_case("grid256_segment", cfg, steps, 5, "l2")
+
+
+def test_grid256_two_segments_match_stored_oracle():
+    """The 256 x 256 four-corner workload's first two checkpoint segments (40 steps) in its
+    own configuration (FP32, CG tol 1e-6, checkpoints every 20 steps: the backward
+    recomputes the first segment from its checkpoint), against the oracle's 40-step run at
+    tol 1e-8 (every 5th vertex stored)."""
+    cfg = W.config5()
+    _single_sheet_case("grid256_two_segments", cfg, 40, cfg.checkpoint_every, "l2")
